@@ -1,0 +1,703 @@
+/*
+ * Oracle for the Monte Carlo assembly of the PDDSparse system G(w) u = b(w)
+ * (arXiv 2301.05780).  TEST INFRASTRUCTURE ONLY: see pdds_oracle.h.
+ *
+ * Everything here is FP64, single-path-at-a-time, in the order the paper states
+ * the method.  Threads split the requested rows; within a row, paths are
+ * simulated and summed in ascending path index, so results do not depend on
+ * the thread count.
+ */
+#include "pdds_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ========================================================================= *
+ * Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   *
+ * easy as 1, 2, 3", SC'11).  Each round multiplies words 0 and 2 by the two  *
+ * round multipliers, and the high halves are xored with the other two words  *
+ * and the round key; the key advances by the two Weyl constants per round.   *
+ * ========================================================================= */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1) from a 32-bit word: (w + 1/2) 2^-32.  Box-Muller (1958):
+ * rho = sqrt(-2 ln u_a), theta = 2 pi u_b, z0 = rho cos theta, z1 = rho sin theta. */
+void orc_box_muller(uint32_t a, uint32_t b, double* z0, double* z1) {
+  const double two32 = 4294967296.0;
+  double ua = ((double)a + 0.5) / two32;
+  double ub = ((double)b + 0.5) / two32;
+  double rho = sqrt(-2.0 * log(ua));
+  double th = 2.0 * M_PI * ub;
+  *z0 = rho * cos(th);
+  *z1 = rho * sin(th);
+}
+
+/* ========================================================================= *
+ * Geometry (Sec. 3.1, Eq. 12-18).                                            *
+ * Omega is the rectangle [x0,x1]x[y0,y1] cut into Hx x Hy subdomains; every   *
+ * subdomain edge carries m knot intervals, so knots live on the integer       *
+ * lattice (i, j), 0 <= i <= LX = Hx m, 0 <= j <= LY = Hy m, on the grid lines  *
+ * (i % m == 0 or j % m == 0).  Unknown knots are the interior ones; knots on   *
+ * the boundary of Omega carry g and are folded into b.  Order: j, then i.     *
+ * ========================================================================= */
+typedef struct {
+  orc_grid g;
+  int LX, LY;
+  double dx, dy;
+  int n;
+  int *ki, *kj;   /* lattice coords of knot k  */
+  int *grid;      /* (LX+1)*(LY+1): knot index or -1 */
+  int64_t nnz;
+  int64_t* row_ptr;
+  int32_t* col;
+} geom_t;
+
+typedef struct {
+  int ilo, ihi, jlo, jhi;  /* patch (slab) box in lattice units, Eq. 13-15 */
+  /* per side O in E,N,W,S: */
+  int dirichlet[4];        /* the side lies on the boundary of Omega       */
+  int line[4];             /* fixed lattice coordinate of the side's line   */
+  int a[4], b[4];          /* stencil lattice range along the line, Eq. 17 */
+} patch_t;
+
+static int is_knot(const geom_t* G, int i, int j) {
+  if (i <= 0 || i >= G->LX || j <= 0 || j >= G->LY) return 0;
+  return (i % G->g.m == 0) || (j % G->g.m == 0);
+}
+
+/* Slab Q(x_k) = union of the closed grid squares whose boundary holds x_k
+ * (Eq. 13).  Omega is a grid-aligned rectangle, so the patch Pi = Q (Eq. 15). */
+static void make_patch(const geom_t* G, int k, patch_t* P) {
+  int m = G->g.m, E = G->g.ext;
+  int i = G->ki[k], j = G->kj[k];
+  if (i % m == 0) { P->ilo = i - m; P->ihi = i + m; }
+  else            { P->ilo = (i / m) * m; P->ihi = P->ilo + m; }
+  if (j % m == 0) { P->jlo = j - m; P->jhi = j + m; }
+  else            { P->jlo = (j / m) * m; P->jhi = P->jlo + m; }
+  /* E: x = ihi, along y.  N: y = jhi, along x.  W: x = ilo.  S: y = jlo. */
+  P->line[0] = P->ihi; P->dirichlet[0] = (P->ihi == G->LX);
+  P->line[1] = P->jhi; P->dirichlet[1] = (P->jhi == G->LY);
+  P->line[2] = P->ilo; P->dirichlet[2] = (P->ilo == 0);
+  P->line[3] = P->jlo; P->dirichlet[3] = (P->jlo == 0);
+  for (int o = 0; o < 4; ++o) {
+    int vertical = (o == 0 || o == 2);
+    int lo = vertical ? P->jlo : P->ilo;
+    int hi = vertical ? P->jhi : P->ihi;
+    int lmax = vertical ? G->LY : G->LX;
+    /* Segment knots plus `ext` knots past each end, kept inside the closure
+     * of Omega (Eq. 17 i-iii; extension as in Fig. 3). */
+    P->a[o] = lo - E < 0 ? 0 : lo - E;
+    P->b[o] = hi + E > lmax ? lmax : hi + E;
+  }
+}
+
+static int cmp_int(const void* a, const void* b) {
+  int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+/* Columns of row k: the knot itself and every unknown knot of its stencils. */
+static int row_columns(const geom_t* G, int k, int* cols) {
+  patch_t P; make_patch(G, k, &P);
+  int nc = 0;
+  cols[nc++] = k;
+  for (int o = 0; o < 4; ++o) {
+    if (P.dirichlet[o]) continue;
+    int vertical = (o == 0 || o == 2);
+    for (int t = P.a[o]; t <= P.b[o]; ++t) {
+      int i = vertical ? P.line[o] : t;
+      int j = vertical ? t : P.line[o];
+      if (is_knot(G, i, j)) cols[nc++] = G->grid[(size_t)j * (G->LX + 1) + i];
+    }
+  }
+  qsort(cols, nc, sizeof(int), cmp_int);
+  int u = 0;
+  for (int q = 0; q < nc; ++q)
+    if (u == 0 || cols[q] != cols[u - 1]) cols[u++] = cols[q];
+  return u;
+}
+
+static void geom_free(geom_t* G) {
+  free(G->ki); free(G->kj); free(G->grid); free(G->row_ptr); free(G->col);
+  memset(G, 0, sizeof(*G));
+}
+
+static int geom_build(const orc_grid* g, geom_t* G, int with_csr) {
+  memset(G, 0, sizeof(*G));
+  if (g->Hx < 1 || g->Hy < 1 || g->m < 1 || g->ext < 0 || !(g->x1 > g->x0) || !(g->y1 > g->y0))
+    return -1;
+  G->g = *g;
+  G->LX = g->Hx * g->m; G->LY = g->Hy * g->m;
+  G->dx = (g->x1 - g->x0) / G->LX;
+  G->dy = (g->y1 - g->y0) / G->LY;
+  size_t np = (size_t)(G->LX + 1) * (G->LY + 1);
+  G->grid = (int*)malloc(np * sizeof(int));
+  int cnt = 0;
+  for (int j = 0; j <= G->LY; ++j)
+    for (int i = 0; i <= G->LX; ++i) {
+      int kk = is_knot(G, i, j) ? cnt++ : -1;
+      G->grid[(size_t)j * (G->LX + 1) + i] = kk;
+    }
+  G->n = cnt;
+  G->ki = (int*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(int));
+  G->kj = (int*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(int));
+  for (int j = 0; j <= G->LY; ++j)
+    for (int i = 0; i <= G->LX; ++i) {
+      int kk = G->grid[(size_t)j * (G->LX + 1) + i];
+      if (kk >= 0) { G->ki[kk] = i; G->kj[kk] = j; }
+    }
+  if (!with_csr) return 0;
+  G->row_ptr = (int64_t*)malloc((size_t)(cnt + 1) * sizeof(int64_t));
+  int maxc = 1 + 4 * (2 * g->m + 2 * g->ext + 1);
+  int* cols = (int*)malloc((size_t)maxc * sizeof(int));
+  G->row_ptr[0] = 0;
+  for (int k = 0; k < cnt; ++k) G->row_ptr[k + 1] = G->row_ptr[k] + row_columns(G, k, cols);
+  G->nnz = G->row_ptr[cnt];
+  G->col = (int32_t*)malloc((size_t)(G->nnz > 0 ? G->nnz : 1) * sizeof(int32_t));
+  for (int k = 0; k < cnt; ++k) {
+    int nc = row_columns(G, k, cols);
+    for (int q = 0; q < nc; ++q) G->col[G->row_ptr[k] + q] = cols[q];
+  }
+  free(cols);
+  return 0;
+}
+
+int orc_geometry_size(const orc_grid* g, int64_t* n, int64_t* nnz) {
+  geom_t G;
+  if (geom_build(g, &G, 1)) return -1;
+  *n = G.n; *nnz = G.nnz;
+  geom_free(&G);
+  return 0;
+}
+
+int orc_geometry(const orc_grid* g, double* xy, int64_t* row_ptr, int32_t* col) {
+  geom_t G;
+  if (geom_build(g, &G, 1)) return -1;
+  for (int k = 0; k < G.n; ++k) {
+    if (xy) {
+      xy[2 * k] = g->x0 + G.ki[k] * G.dx;
+      xy[2 * k + 1] = g->y0 + G.kj[k] * G.dy;
+    }
+  }
+  if (row_ptr) memcpy(row_ptr, G.row_ptr, (size_t)(G.n + 1) * sizeof(int64_t));
+  if (col) memcpy(col, G.col, (size_t)G.nnz * sizeof(int32_t));
+  geom_free(&G);
+  return 0;
+}
+
+/* ========================================================================= *
+ * Coefficients of Eq. 6 (sigma = s I, so A = s^2 I and the generator is       *
+ * (s^2/2) Lap + d . grad), and the boundary data g.                           *
+ * ========================================================================= */
+static double table_bilinear(const orc_grid* g, const float* T, int nx, int ny, double x, double y) {
+  double fx = (x - g->x0) / (g->x1 - g->x0) * (nx - 1);
+  double fy = (y - g->y0) / (g->y1 - g->y0) * (ny - 1);
+  int i = (int)floor(fx), j = (int)floor(fy);
+  if (i < 0) i = 0;
+  if (i > nx - 2) i = nx - 2;
+  if (j < 0) j = 0;
+  if (j > ny - 2) j = ny - 2;
+  double tx = fx - i, ty = fy - j;
+  double v00 = T[(size_t)j * nx + i], v10 = T[(size_t)j * nx + i + 1];
+  double v01 = T[(size_t)(j + 1) * nx + i], v11 = T[(size_t)(j + 1) * nx + i + 1];
+  return (1 - tx) * (1 - ty) * v00 + tx * (1 - ty) * v10 + (1 - tx) * ty * v01 + tx * ty * v11;
+}
+
+void orc_coeffs_eval(const orc_grid* g, const orc_coeffs* cf, double x, double y,
+                     double* s, double* dx, double* dy, double* c, double* f) {
+  const double pi = M_PI;
+  switch (cf->id) {
+  case ORC_COEF_LAPLACE_EXPSIN:
+    *s = sqrt(2.0); *dx = 0; *dy = 0; *c = 0; *f = 0;
+    break;
+  case ORC_COEF_MANUFACTURED: {
+    /* u = sin(pi x) cos(pi y) + x y;  Lap u = -2 pi^2 sin(pi x) cos(pi y). */
+    double sx = sin(pi * x), cx = cos(pi * x), sy = sin(pi * y), cy = cos(pi * y);
+    double u = sx * cy + x * y;
+    double ux = pi * cx * cy + y;
+    double uy = -pi * sx * sy + x;
+    double lap = -2.0 * pi * pi * sx * cy;
+    *s = sqrt(2.0);
+    *dx = sin(2.0 * pi * y);
+    *dy = cos(2.0 * pi * x);
+    *c = -(1.0 + x * x);
+    *f = lap + (*dx) * ux + (*dy) * uy + (*c) * u;  /* (s^2/2) = 1 */
+    break;
+  }
+  case ORC_COEF_VARSIGMA: {
+    /* u = e^{x/4} cos(y/2);  Lap u = (1/16 - 1/4) u. */
+    double sg = sqrt(2.0) * (1.0 + 0.3 * sin(2.0 * pi * x) * sin(2.0 * pi * y));
+    double u = exp(x / 4.0) * cos(y / 2.0);
+    *s = sg; *dx = 0; *dy = 0; *c = -1.0;
+    *f = 0.5 * sg * sg * (1.0 / 16.0 - 1.0 / 4.0) * u + (*c) * u;
+    break;
+  }
+  case ORC_COEF_TABLE:
+    *s = table_bilinear(g, cf->sigma_tab, cf->tab_nx, cf->tab_ny, x, y);
+    *c = table_bilinear(g, cf->c_tab, cf->tab_nx, cf->tab_ny, x, y);
+    *dx = 0; *dy = 0; *f = cf->params[0];
+    break;
+  default: /* ORC_COEF_CONSTANT */
+    *s = cf->params[0]; *dx = cf->params[1]; *dy = cf->params[2];
+    *c = cf->params[3]; *f = cf->params[4];
+    break;
+  }
+}
+
+double orc_boundary_g(const orc_coeffs* cf, double x, double y) {
+  const double pi = M_PI;
+  switch (cf->id) {
+  case ORC_COEF_LAPLACE_EXPSIN: return exp(x) * sin(y);
+  case ORC_COEF_MANUFACTURED:   return sin(pi * x) * cos(pi * y) + x * y;
+  case ORC_COEF_VARSIGMA:       return exp(x / 4.0) * cos(y / 2.0);
+  case ORC_COEF_TABLE:          return cf->params[1];
+  default:                      return cf->params[5];
+  }
+}
+
+/* ========================================================================= *
+ * v_theta : R^2 -> R, 2 -> 64 -> 64 -> 1 with SiLU (a * logistic(a)).         *
+ * theta layout: W1[64][2], b1[64], W2[64][64] (row = output), b2[64], w3[64], *
+ * b3.                                                                         *
+ * ========================================================================= */
+#define HID ORC_MLP_HIDDEN
+static double logistic(double a) { return 1.0 / (1.0 + exp(-a)); }
+
+typedef struct { double a1[HID], h1[HID], a2[HID], h2[HID], v; } mlp_fwd_t;
+
+static void mlp_forward(const double* th, double x, double y, mlp_fwd_t* F) {
+  const double *W1 = th, *b1 = W1 + 2 * HID, *W2 = b1 + HID, *b2 = W2 + HID * HID,
+               *w3 = b2 + HID, *b3 = w3 + HID;
+  for (int i = 0; i < HID; ++i) {
+    F->a1[i] = W1[2 * i] * x + W1[2 * i + 1] * y + b1[i];
+    F->h1[i] = F->a1[i] * logistic(F->a1[i]);
+  }
+  for (int i = 0; i < HID; ++i) {
+    double s = b2[i];
+    for (int j = 0; j < HID; ++j) s += W2[i * HID + j] * F->h1[j];
+    F->a2[i] = s;
+    F->h2[i] = s * logistic(s);
+  }
+  double v = b3[0];
+  for (int i = 0; i < HID; ++i) v += w3[i] * F->h2[i];
+  F->v = v;
+}
+
+/* d/da [a logistic(a)] = logistic(a) (1 + a (1 - logistic(a))). */
+static double dsilu(double a) { double s = logistic(a); return s * (1.0 + a * (1.0 - s)); }
+
+double orc_mlp_value(const double* th, double x, double y) {
+  mlp_fwd_t F; mlp_forward(th, x, y, &F); return F.v;
+}
+
+void orc_mlp_grad_x(const double* th, double x, double y, double* gx, double* gy) {
+  const double *W1 = th, *b1 = W1 + 2 * HID, *W2 = b1 + HID, *b2 = W2 + HID * HID, *w3 = b2 + HID;
+  mlp_fwd_t F; mlp_forward(th, x, y, &F);
+  double g2[HID], g1[HID];
+  for (int i = 0; i < HID; ++i) g2[i] = w3[i] * dsilu(F.a2[i]);            /* dv/da2 */
+  for (int j = 0; j < HID; ++j) {                                           /* dv/da1 */
+    double s = 0;
+    for (int i = 0; i < HID; ++i) s += W2[i * HID + j] * g2[i];
+    g1[j] = s * dsilu(F.a1[j]);
+  }
+  double sx = 0, sy = 0;
+  for (int j = 0; j < HID; ++j) { sx += W1[2 * j] * g1[j]; sy += W1[2 * j + 1] * g1[j]; }
+  *gx = sx; *gy = sy;
+}
+
+double orc_mlp_loss_grad(const double* th, const double* xy, const double* target,
+                         int64_t npts, double* grad) {
+  const double *W2 = th + 2 * HID + HID, *w3 = W2 + HID * HID + HID;
+  double *gW1 = grad, *gb1 = gW1 + 2 * HID, *gW2 = gb1 + HID, *gb2 = gW2 + HID * HID,
+         *gw3 = gb2 + HID, *gb3 = gw3 + HID;
+  memset(grad, 0, sizeof(double) * ORC_MLP_NPARAM);
+  double loss = 0;
+  for (int64_t p = 0; p < npts; ++p) {
+    double x = xy[2 * p], y = xy[2 * p + 1];
+    mlp_fwd_t F; mlp_forward(th, x, y, &F);
+    double r = F.v - target[p];
+    loss += r * r;
+    double dv = 2.0 * r / (double)npts;                   /* dL/dv */
+    double d2[HID], d1[HID];
+    gb3[0] += dv;
+    for (int i = 0; i < HID; ++i) { gw3[i] += dv * F.h2[i]; d2[i] = dv * w3[i] * dsilu(F.a2[i]); }
+    for (int i = 0; i < HID; ++i) {
+      gb2[i] += d2[i];
+      for (int j = 0; j < HID; ++j) gW2[i * HID + j] += d2[i] * F.h1[j];
+    }
+    for (int j = 0; j < HID; ++j) {
+      double s = 0;
+      for (int i = 0; i < HID; ++i) s += W2[i * HID + j] * d2[i];
+      d1[j] = s * dsilu(F.a1[j]);
+      gb1[j] += d1[j];
+      gW1[2 * j] += d1[j] * x;
+      gW1[2 * j + 1] += d1[j] * y;
+    }
+  }
+  return loss / (double)npts;
+}
+
+void orc_adam_step(double* th, const double* g, double* m, double* v, int64_t t,
+                   int64_t np, double lr, double b1, double b2, double eps) {
+  double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int64_t i = 0; i < np; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    th[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
+/* ========================================================================= *
+ * One Feynman-Kac path inside the patch of knot k (Eq. 9, naive EM, Sec. 2.3) *
+ * and its exit resolution (Eq. 22-25, corner rule of Sec. 3.3).               *
+ * ========================================================================= */
+typedef struct {
+  const geom_t* G;
+  const orc_coeffs* cf;
+  double h, sqh;
+  uint32_t key[2];
+  uint32_t tag;
+  int64_t k_max;
+} sim_t;
+
+typedef struct {
+  int steps, side, flags;
+  int col[2];          /* unknown-knot columns, -1 if none */
+  double w[2];         /* Y * interpolation weight for col[]  */
+  double bsum;         /* everything that goes to b           */
+  double Y;
+} path_out_t;
+
+static void simulate_path(const sim_t* S, int k, int64_t p, path_out_t* out) {
+  const geom_t* G = S->G;
+  const orc_grid* g = &G->g;
+  patch_t P; make_patch(G, k, &P);
+  double xlo = g->x0 + P.ilo * G->dx, xhi = g->x0 + P.ihi * G->dx;
+  double ylo = g->y0 + P.jlo * G->dy, yhi = g->y0 + P.jhi * G->dy;
+  double X = g->x0 + G->ki[k] * G->dx, Yp = g->y0 + G->kj[k] * G->dy;
+  double Sacc = 0.0, Z = 0.0, xi = 0.0;   /* Y = exp(S) */
+  int64_t n = 0;
+  int truncated = 0;
+  double z[4] = {0, 0, 0, 0};
+  for (;;) {
+    if ((n & 1) == 0) {
+      /* One Philox call per two steps: counter (step pair, path, knot, tag). */
+      uint32_t ctr[4] = {(uint32_t)(n >> 1), (uint32_t)p, (uint32_t)k, S->tag}, r[4];
+      orc_philox4x32_10(ctr, S->key, r);
+      orc_box_muller(r[0], r[1], &z[0], &z[1]);
+      orc_box_muller(r[2], r[3], &z[2], &z[3]);
+    }
+    double zx = z[(n & 1) * 2], zy = z[(n & 1) * 2 + 1];
+    double s, dxv, dyv, c, f;
+    orc_coeffs_eval(g, S->cf, X, Yp, &s, &dxv, &dyv, &c, &f);
+    double Yw = exp(Sacc);
+    double dWx = S->sqh * zx, dWy = S->sqh * zy;
+    Z -= f * Yw * S->h;                                  /* dZ = -f Y dt      */
+    if (S->cf->mlp) {                                    /* dxi = -Y F . dW   */
+      double gx, gy;
+      orc_mlp_grad_x(S->cf->mlp, X, Yp, &gx, &gy);
+      xi -= Yw * s * (gx * dWx + gy * dWy);              /* F = sigma^T grad v */
+    }
+    Sacc += c * S->h;                                    /* dY = c Y dt       */
+    X += dxv * S->h + s * dWx;                           /* dX = d dt + s dW  */
+    Yp += dyv * S->h + s * dWy;
+    ++n;
+    if (X > xhi || X < xlo || Yp > yhi || Yp < ylo) break;   /* left closed patch */
+    if (n >= S->k_max) { truncated = 1; break; }
+  }
+  double Yk = exp(Sacc);
+  /* Signed overshoot past each side, E N W S. */
+  double ov[4] = {X - xhi, Yp - yhi, xlo - X, ylo - Yp};
+  int side = -1;
+  for (int o = 0; o < 4; ++o)          /* smallest positive overshoot */
+    if (ov[o] > 0 && (side < 0 || ov[o] < ov[side])) side = o;
+  if (side < 0)                         /* truncated inside: nearest side */
+    for (int o = 0; o < 4; ++o)
+      if (side < 0 || ov[o] > ov[side]) side = o;
+
+  out->steps = (int)n;
+  out->side = side;
+  out->flags = truncated ? 1 : 0;
+  out->col[0] = out->col[1] = -1;
+  out->w[0] = out->w[1] = 0;
+  out->Y = Yk;
+  double bsum = Z + xi;
+  int vertical = (side == 0 || side == 2);
+  double line_xy = vertical ? (side == 0 ? xhi : xlo) : (side == 1 ? yhi : ylo);
+  double along = vertical ? Yp : X;
+  if (P.dirichlet[side]) {
+    /* Exit on the boundary of Omega: score g(P) Y (Eq. 25), P projected
+     * normally and kept in the closure of Omega. */
+    double lo = vertical ? g->y0 : g->x0, hi = vertical ? g->y1 : g->x1;
+    if (along < lo) along = lo;
+    if (along > hi) along = hi;
+    double px = vertical ? line_xy : along, py = vertical ? along : line_xy;
+    bsum += Yk * orc_boundary_g(S->cf, px, py);
+  } else {
+    /* Exit on an interface: piecewise-linear interpolation over the side's
+     * extended stencil (Eq. 21-22 with a linear scheme, footnote 8). */
+    double origin = vertical ? g->y0 : g->x0, step = vertical ? G->dy : G->dx;
+    int lmax = vertical ? G->LY : G->LX;
+    double s = (along - origin) / step;
+    if (s < P.a[side]) { s = P.a[side]; out->flags |= 2; }
+    if (s > P.b[side]) { s = P.b[side]; out->flags |= 2; }
+    int t = (int)floor(s);
+    if (t >= P.b[side]) t = P.b[side] - 1;
+    double lam = s - t;
+    double w[2] = {1.0 - lam, lam};
+    for (int q = 0; q < 2; ++q) {
+      int tl = t + q;
+      int i = vertical ? P.line[side] : tl;
+      int j = vertical ? tl : P.line[side];
+      if (tl == 0 || tl == lmax) {
+        /* Stencil end on the boundary of Omega: known value g there. */
+        bsum += Yk * w[q] * orc_boundary_g(S->cf, g->x0 + i * G->dx, g->y0 + j * G->dy);
+      } else {
+        out->col[q] = G->grid[(size_t)j * (G->LX + 1) + i];
+        out->w[q] = Yk * w[q];
+      }
+    }
+  }
+  out->bsum = bsum;
+}
+
+/* ========================================================================= *
+ * Row assembly (Eq. 24-25).  Raw sums: val holds sum_p Y w for each column,   *
+ * b holds sum_p of the b contributions; orc_finalize_rows divides by N_k.     *
+ * ========================================================================= */
+typedef struct {
+  sim_t S;
+  const int64_t* n_per_knot;
+  int64_t n_paths;
+  const int32_t* rows;
+  int32_t nrows;
+  double* val;
+  double* b;
+  orc_record* records;
+  const int64_t* rec_off;     /* record offset per requested row */
+  int next;                    /* shared row counter */
+  pthread_mutex_t mu;
+  int64_t stats[3];
+} job_t;
+
+static int64_t paths_of(const job_t* J, int k) {
+  return J->n_per_knot ? J->n_per_knot[k] : J->n_paths;
+}
+
+static void assemble_row(job_t* J, int r, int64_t* st) {
+  const geom_t* G = J->S.G;
+  int k = J->rows[r];
+  int64_t N = paths_of(J, k);
+  int64_t rb = G->row_ptr[k], re = G->row_ptr[k + 1];
+  int nc = (int)(re - rb);
+  double* acc = (double*)calloc((size_t)nc, sizeof(double));
+  double bacc = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    path_out_t o;
+    simulate_path(&J->S, k, p, &o);
+    st[0] += o.steps;
+    st[1] += (o.flags & 1) ? 1 : 0;
+    st[2] += (o.flags & 2) ? 1 : 0;
+    for (int q = 0; q < 2; ++q) {
+      if (o.col[q] < 0) continue;
+      int lo = 0, hi = nc - 1, pos = -1;       /* column search in the row */
+      while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        int cm = G->col[rb + mid];
+        if (cm == o.col[q]) { pos = mid; break; }
+        if (cm < o.col[q]) lo = mid + 1; else hi = mid - 1;
+      }
+      if (pos >= 0) acc[pos] += o.w[q];
+    }
+    bacc += o.bsum;
+    if (J->records) {
+      orc_record* R = &J->records[J->rec_off[r] + p];
+      R->steps = o.steps; R->side = o.side; R->flags = o.flags;
+      R->col_a = o.col[0]; R->col_b = o.col[1]; R->pad_ = 0;
+      R->w_a = o.w[0]; R->w_b = o.w[1]; R->b_contrib = o.bsum; R->Y = o.Y;
+    }
+  }
+  for (int q = 0; q < nc; ++q) J->val[rb + q] = acc[q];
+  J->b[k] = bacc;
+  free(acc);
+}
+
+static void* worker(void* arg) {
+  job_t* J = (job_t*)arg;
+  int64_t st[3] = {0, 0, 0};
+  for (;;) {
+    pthread_mutex_lock(&J->mu);
+    int r = J->next++;
+    pthread_mutex_unlock(&J->mu);
+    if (r >= J->nrows) break;
+    assemble_row(J, r, st);
+  }
+  pthread_mutex_lock(&J->mu);
+  for (int i = 0; i < 3; ++i) J->stats[i] += st[i];
+  pthread_mutex_unlock(&J->mu);
+  return NULL;
+}
+
+int orc_assemble(const orc_grid* g, const orc_coeffs* cf,
+                 const int64_t* n_per_knot, int64_t n_paths,
+                 double dt, uint64_t seed, uint32_t tag_word, int64_t k_max,
+                 const int32_t* rows, int32_t nrows, int32_t threads,
+                 double* val, double* b, orc_record* records, int64_t* stats) {
+  if (!(dt > 0) || k_max < 1) return -1;
+  geom_t G;
+  if (geom_build(g, &G, 1)) return -1;
+  for (int r = 0; r < nrows; ++r)
+    if (rows[r] < 0 || rows[r] >= G.n) { geom_free(&G); return -2; }
+  job_t J;
+  memset(&J, 0, sizeof(J));
+  J.S.G = &G; J.S.cf = cf; J.S.h = dt; J.S.sqh = sqrt(dt);
+  J.S.key[0] = (uint32_t)seed; J.S.key[1] = (uint32_t)(seed >> 32);
+  J.S.tag = tag_word; J.S.k_max = k_max;
+  J.n_per_knot = n_per_knot; J.n_paths = n_paths;
+  J.rows = rows; J.nrows = nrows; J.val = val; J.b = b; J.records = records;
+  int64_t* off = NULL;
+  if (records) {
+    off = (int64_t*)malloc((size_t)(nrows + 1) * sizeof(int64_t));
+    off[0] = 0;
+    for (int r = 0; r < nrows; ++r) off[r + 1] = off[r] + paths_of(&J, rows[r]);
+    J.rec_off = off;
+  }
+  pthread_mutex_init(&J.mu, NULL);
+  if (threads < 1) threads = 1;
+  pthread_t* th = (pthread_t*)malloc((size_t)threads * sizeof(pthread_t));
+  for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, worker, &J);
+  for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  pthread_mutex_destroy(&J.mu);
+  if (stats) for (int i = 0; i < 3; ++i) stats[i] += J.stats[i];
+  free(off);
+  geom_free(&G);
+  return 0;
+}
+
+void orc_finalize_rows(const orc_grid* g, const int64_t* row_ptr, const int32_t* col,
+                       const int64_t* n_per_knot, int64_t n_paths,
+                       const int32_t* rows, int32_t nrows, double* val, double* b) {
+  (void)g;
+  for (int r = 0; r < nrows; ++r) {
+    int k = rows[r];
+    double N = (double)(n_per_knot ? n_per_knot[k] : n_paths);
+    for (int64_t q = row_ptr[k]; q < row_ptr[k + 1]; ++q)
+      val[q] = (col[q] == k) ? 1.0 : -val[q] / N;       /* Eq. 24 */
+    b[k] = b[k] / N;                                     /* Eq. 25 */
+  }
+}
+
+/* ========================================================================= *
+ * Linear solves for Eq. 23.                                                   *
+ * ========================================================================= */
+int orc_lu_solve(int64_t n, const double* A_in, const double* b, double* x) {
+  /* Gaussian elimination with partial pivoting on a copy. */
+  double* A = (double*)malloc((size_t)(n * n) * sizeof(double));
+  double* r = (double*)malloc((size_t)n * sizeof(double));
+  memcpy(A, A_in, (size_t)(n * n) * sizeof(double));
+  memcpy(r, b, (size_t)n * sizeof(double));
+  int rc = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t piv = c;
+    for (int64_t i = c + 1; i < n; ++i)
+      if (fabs(A[i * n + c]) > fabs(A[piv * n + c])) piv = i;
+    if (A[piv * n + c] == 0.0) { rc = -1; break; }
+    if (piv != c) {
+      for (int64_t j = 0; j < n; ++j) { double t = A[c * n + j]; A[c * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+      double t = r[c]; r[c] = r[piv]; r[piv] = t;
+    }
+    for (int64_t i = c + 1; i < n; ++i) {
+      double l = A[i * n + c] / A[c * n + c];
+      if (l == 0.0) continue;
+      for (int64_t j = c; j < n; ++j) A[i * n + j] -= l * A[c * n + j];
+      r[i] -= l * r[c];
+    }
+  }
+  if (rc == 0)
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = r[i];
+      for (int64_t j = i + 1; j < n; ++j) s -= A[i * n + j] * x[j];
+      x[i] = s / A[i * n + i];
+    }
+  free(A); free(r);
+  return rc;
+}
+
+static void spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                 const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) s += v[q] * x[ci[q]];
+    y[i] = s;
+  }
+}
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* BiCGSTAB (van der Vorst 1992), x0 = 0, stop at ||r|| <= rtol ||b||. */
+int orc_bicgstab(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                 const double* b, double* x, double rtol, int32_t maxit, int32_t* iters,
+                 double* relres) {
+  double *r = calloc(n, 8), *rh = calloc(n, 8), *p = calloc(n, 8), *v = calloc(n, 8),
+         *s = calloc(n, 8), *t = calloc(n, 8);
+  for (int64_t i = 0; i < n; ++i) { x[i] = 0; r[i] = b[i]; rh[i] = b[i]; }
+  double bn = sqrt(dot(n, b, b));
+  if (bn == 0) bn = 1;
+  double rho = 1, alpha = 1, omega = 1;
+  int it = 0, rc = -1;
+  double res = sqrt(dot(n, r, r)) / bn;
+  if (res <= rtol) rc = 0;
+  while (rc != 0 && it < maxit) {
+    ++it;
+    double rho1 = dot(n, rh, r);
+    if (rho1 == 0) break;
+    double beta = (rho1 / rho) * (alpha / omega);
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    spmv(n, rp, ci, val, p, v);
+    alpha = rho1 / dot(n, rh, v);
+    for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+    double sn = sqrt(dot(n, s, s)) / bn;
+    if (sn <= rtol) {
+      for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+      res = sn; rc = 0; break;
+    }
+    spmv(n, rp, ci, val, s, t);
+    omega = dot(n, t, s) / dot(n, t, t);
+    for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i] + omega * s[i]; r[i] = s[i] - omega * t[i]; }
+    rho = rho1;
+    res = sqrt(dot(n, r, r)) / bn;
+    if (res <= rtol) rc = 0;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = res;
+  free(r); free(rh); free(p); free(v); free(s); free(t);
+  return rc;
+}
