@@ -1,0 +1,349 @@
+"""Benchmark of the PDDSparse hot path on GB300: Monte Carlo assembly of
+G(w) u = b(w) (Eq. 24-25) plus its FP64 solve (Eq. 23), on the config-2
+workload (manufactured u = sin(pi x)cos(pi y) + xy on [0,1]^2, 8x8 subdomains,
+833 knots, N = 1e5 paths per knot, dt = 1e-5).
+
+One step = one full assemble + solve of that system.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config cfg2]
+
+N > 1 runs under torchrun, one process per GPU; every rank assembles an
+independent replica (its own seed), so per-GPU work is fixed (weak scaling)
+and no collective touches the data path (a barrier and a max-reduction of the
+timings only).  ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Counted FP32 operations per Euler-Maruyama path-step of the path kernel
+# (FMA = 2, every other FP32 add/mul/compare/min/max = 1, each hardware
+# transcendental = 1), read off paper_2301_05780_gb300/csrc/pdds_path.cu:
+#   Box-Muller share per step 17, exit test 4, EM update 17 (with Y, Z) or 6,
+#   coefficients: MANUFACTURED 39, VARSIGMA 32, TABLE 26 (two bilinear lookups), LAPLACE 0,
+#   CONSTANT 0.
+FLOPS_PER_STEP = {0: 27, 1: 77, 2: 70, 3: 64, 4: 38}
+SMS_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2301_05780_gb300", "csrc", "pdds_path.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the path kernel from the committed ncu summary,
+    if the summary was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "path_kernel_cfg2_ncu.txt")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_b) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank r's independent replica (rank 0 keeps the workload seed)."""
+    return (base + 1000003 * rank) % 2**64
+
+
+def reduce_timing(total_ms: float, path_steps: float, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of the
+    path-steps all ranks processed (timing only; no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, path_steps
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    s = torch.tensor([path_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(s[0])
+
+
+def workload(name: str):
+    from paper_2301_05780_gb300 import workloads as W
+    return W.all_configs()[name]()
+
+
+# ------------------------------------------------------------------ CPU arm
+def oracle_sample(w, rows_wanted: int, threads: int):
+    """Times the FP64 oracle on `rows_wanted` evenly spaced rows of w at the
+    full per-knot budget; returns (path_steps, seconds, rows)."""
+    import oracle
+    O = oracle.Problem(w.grid, w.coef_id, w.params)
+    rows = np.linspace(0, O.n - 1, rows_wanted).round().astype(np.int32)
+    t0 = time.perf_counter()
+    _, _, st, _ = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, rows=rows, threads=threads)
+    return int(st[0]), time.perf_counter() - t0, rows
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    threads = os.cpu_count() or 1
+    steps, secs, rows = oracle_sample(w, threads, threads)       # calibration
+    rate = steps / secs
+    per_row = steps / len(rows)
+    want = int(max(threads, min(w.extra.get("n_rows", 10**9), budget_s * rate / per_row)))
+    want = min(want, 400)
+    steps, secs, rows = oracle_sample(w, want, threads)
+    return {"value": steps / secs, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(rows)} evenly spaced rows of {w.name} at N={w.n_paths}, "
+                      f"dt={w.dt:g} ({steps:.3e} path-steps in {secs:.1f} s, FP64, "
+                      f"{threads} threads)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.config)
+    threads = os.cpu_count() or 1
+    rows_per_step = max(threads, 2 * threads)
+    for _ in range(args.warmup):
+        oracle_sample(w, threads, threads)
+    tot_steps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        s, t, rows = oracle_sample(w, rows_per_step, threads)
+        tot_steps += s
+        tot_s += t
+    v = tot_steps / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "path-steps/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample_rows_per_step": rows_per_step,
+                       "paths_per_knot": w.n_paths, "dt": w.dt},
+            "cpu_baseline": {"value": v, "unit": "path-steps/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{rows_per_step} evenly spaced rows per step of {w.name} "
+                                       f"at N={w.n_paths} (FP64 oracle, {threads} threads)"},
+            "e2e": {"value": v, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+METRIC = "path-steps/s & G,b assembly time at fixed interface RMS error; % of FP32 peak"
+
+
+def run_gpu(args):
+    import torch
+    from paper_2301_05780_gb300 import pdds
+
+    rank, local, world = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.config)
+    w.seed = replica_seed(w.seed, rank)       # independent replica per rank
+    P = pdds.Problem(w, device=local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    pdds.pdds_set_timing(P.ctx, True)
+
+    def step():
+        P.assemble(stream)
+        st = pdds.pdds_stats(P.ctx)
+        P.solve(rtol=1e-12, maxit=5000, stream=stream)
+        st2 = pdds.pdds_stats(P.ctx)
+        return st, st2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    path_ms, steps_done, launches, errors, iters = [], 0, 0, 0, []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()                    # evict L2 between timed steps
+            ev[i][0].record(stream)
+            st, st2 = step()
+            ev[i][1].record(stream)
+            path_ms.append(st["path_kernel_ms"])
+            steps_done += st["path_steps"]
+            launches += st2["kernel_launches"]
+            errors += st["device_error"]
+            iters.append(st2["solve_iters"])
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    total_ms_max, steps_all = reduce_timing(total_ms, float(steps_done), device="cuda")
+    value = steps_all / (total_ms_max * 1e-3)
+
+    # ---- end to end through the host-buffer C-ABI call (pinned buffers)
+    n, nnz = P.n, P.nnz
+    pin = dict(pin_memory=True)
+    Nh = torch.full((n,), w.n_paths, dtype=torch.int64, **pin)
+    rp = torch.empty(n + 1, dtype=torch.int32, **pin)
+    col = torch.empty(nnz, dtype=torch.int32, **pin)
+    val = torch.empty(nnz, dtype=torch.float64, **pin)
+    bh = torch.empty(n, dtype=torch.float64, **pin)
+    uh = torch.empty(n, dtype=torch.float64, **pin)
+    pdds.pdds_set_timing(P.ctx, False)
+    e2e_steps = max(2, min(args.steps, 5))
+    pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 5000, rp, col, val, bh, uh,
+                                  n_per_knot=Nh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 5000, rp, col, val, bh, uh,
+                                      n_per_knot=Nh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = steps_done / args.steps / e2e_s * world
+    h2d = n * 8
+    d2h = (n + 1) * 4 + nnz * 4 + nnz * 8 + 2 * n * 8
+
+    # interface error against the manufactured solution (last timed step)
+    xy = pdds.pdds_knot_coords(P.ctx)
+    u = P.u.cpu().numpy()
+    ex = np.sin(np.pi * xy[:, 0]) * np.cos(np.pi * xy[:, 1]) + xy[:, 0] * xy[:, 1]
+    rms = float(np.sqrt(np.mean((u - ex) ** 2)))
+
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    peaks, src = measured_peaks()
+    clk_s = clk.summary()
+    fpk = FLOPS_PER_STEP[w.coef_id]
+    kernel_s = float(np.mean(path_ms)) * 1e-3
+    flops_launch = steps_done / args.steps * fpk
+    achieved = flops_launch / kernel_s / 1e12
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    cpu = cpu_baseline(w) if world == 1 or rank == 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "knots": n, "paths_per_knot": w.n_paths, "dt": w.dt,
+                   "path_steps_per_step": steps_done / args.steps,
+                   "assembly_ms": float(np.mean(path_ms)),
+                   "solve_iters": int(np.median(iters)), "interface_rms_error": rms,
+                   "accumulation": "f64", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(w.name),
+                     "kernel": "path_kernel", "flops_per_path_step": fpk,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                    f"({src} max SM clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk_s,
+        "device_errors": errors,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg4", "cfg5"])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

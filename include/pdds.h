@@ -1,0 +1,222 @@
+/*
+ * pdds.h -- C ABI of the GB300 (sm_103a) PDDSparse assembly library.
+ *
+ * PDDSparse (Bernal, Moron-Vidal & Acebron, arXiv 2301.05780) turns a 2-D
+ * linear elliptic Dirichlet problem (Eq. 6) on a domain cut into square
+ * subdomains into a sparse "interfacial" system G(w) u = b(w) (Eq. 23) whose
+ * unknowns are the solution values at knots on the subdomain interfaces
+ * (Sec. 3.1).  Row k of G and b_k are Monte Carlo expectations over
+ * Feynman-Kac paths started at knot k and stopped when they leave the knot's
+ * patch (Eq. 19-25); this library computes them on one GPU and solves the
+ * system.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a pdds_status; no exception crosses the ABI.  On
+ *    failure the context's error text (pdds_last_error) says why; failures
+ *    before a context exists are described by pdds_last_error(NULL).
+ *  - "device" pointers are CUDA device (or managed) memory on the current
+ *    device; "host" pointers are ordinary host memory.  Caller-owned buffers
+ *    are borrowed for the duration of the call only, unless stated otherwise.
+ *  - Work is enqueued on the CUDA stream passed as `cuda_stream`
+ *    (a cudaStream_t; NULL = legacy default stream) and is asynchronous with
+ *    respect to the host, unless the entry point says it synchronizes.
+ *  - Knot order is lexicographic in (y, x) over the interior knots, i.e. the
+ *    knots on interior grid lines that are not on the boundary of Omega.  Knots
+ *    on the boundary are not unknowns: their known values g enter b.
+ *  - CSR matrices use int32 row pointers / column indices, columns ascending
+ *    within a row, the diagonal included.
+ */
+#ifndef PDDS_H
+#define PDDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PDDS_OK = 0,
+  PDDS_EINVAL = 1,   /* invalid argument (size, pointer, range)                      */
+  PDDS_ENOMEM = 2,   /* device or host allocation failed                             */
+  PDDS_ECUDA = 3,    /* a CUDA runtime call failed (text in pdds_last_error)         */
+  PDDS_ENOCONV = 4,  /* the iterative solve hit maxit before reaching rtol            */
+  PDDS_ETIMEOUT = 5, /* a bounded device-side wait gave up (reported by pdds_stats)   */
+  PDDS_ETRUNC = 6    /* informational: some paths reached the step cap                */
+} pdds_status;
+
+typedef struct pdds_ctx pdds_ctx; /* opaque; owns the device-side problem tables */
+
+/* Domain and its subdomain grid (Sec. 3.1, Eq. 12-18).
+ * Omega = [x0,x1] x [y0,y1] is cut into Hx x Hy equal rectangles; every
+ * subdomain edge carries m knot intervals.  `ext` knots are added to each
+ * patch-side stencil past both segment ends (clipped to the closure of
+ * Omega), so that a diagonal overshoot near a patch corner can be projected
+ * on the extended stencil instead of onto the corner (Sec. 3.3, Fig. 3). */
+typedef struct {
+  double x0, x1, y0, y1;
+  int32_t Hx, Hy; /* >= 1 each, and Hx >= 2 or Hy >= 2 (otherwise no knots)   */
+  int32_t m;      /* >= 1                                                     */
+  int32_t ext;    /* >= 0                                                     */
+} pdds_grid;
+
+/* Coefficients of Eq. 6 with diffusion sigma(x) = s(x) I (so A = s^2 I).
+ * Built-in sets (kind = PDDS_COEF_BUILTIN, builtin_id):                        */
+enum {
+  PDDS_COEF_LAPLACE_EXPSIN = 0, /* s = sqrt2, d = 0, c = 0, f = 0, g = e^x sin y      */
+  PDDS_COEF_MANUFACTURED = 1,   /* s = sqrt2, d = (sin 2pi y, cos 2pi x), c = -(1+x^2),
+                                   f = L u for u = sin(pi x)cos(pi y) + x y, g = u      */
+  PDDS_COEF_VARSIGMA = 2,       /* s = sqrt2 (1 + 0.3 sin 2pi x sin 2pi y), d = 0, c = -1,
+                                   f = L u for u = e^{x/4} cos(y/2), g = u              */
+  PDDS_COEF_TABLE = 3,          /* s and c bilinear in FP32 tables, d = 0,
+                                   f = params[0], g = params[1] (constants)           */
+  PDDS_COEF_CONSTANT = 4        /* s = p0, d = (p1, p2), c = p3, f = p4, g = p5        */
+};
+enum { PDDS_COEF_BUILTIN = 0 };
+
+typedef struct {
+  int32_t kind;         /* PDDS_COEF_BUILTIN                                          */
+  int32_t builtin_id;   /* PDDS_COEF_*                                                 */
+  const float* sigma_tab; /* TABLE only: host or device, [tab_ny][tab_nx] row-major,    */
+  const float* c_tab;     /*   nodes spanning Omega; copied at pdds_create (not kept)   */
+  int32_t tab_nx, tab_ny; /* >= 2 each                                                  */
+  double params[8];
+} pdds_coeffs;
+
+/* CSR matrix in caller-owned DEVICE memory: row_ptr[n+1], col[nnz], val[nnz]. */
+typedef struct {
+  int64_t n, nnz;
+  int32_t* row_ptr;
+  int32_t* col;
+  double* val;
+} pdds_csr;
+
+/* Per-path record written by pdds_assemble_records (32 bytes). */
+typedef struct {
+  int32_t steps;      /* K, Euler-Maruyama steps taken                                */
+  int32_t side_flags; /* exit side (0 E, 1 N, 2 W, 3 S) | flags << 8: bit0 step cap,
+                         bit1 along-line clamp                                         */
+  int32_t col_a, col_b; /* knots receiving w_a, w_b; -1 = none or boundary point      */
+  float w_a, w_b;     /* Y_K times the interpolation weight                           */
+  float b_contrib;    /* Z_K + xi_K + boundary terms: the path's share of b_k times N */
+  float Y;            /* Y_K = exp(int c dt)                                          */
+} pdds_path_record;
+
+typedef struct {
+  int64_t path_steps;       /* sum over paths of K (last assemble call)                */
+  int64_t paths;            /* paths completed                                         */
+  int64_t truncated;        /* paths that reached the step cap                          */
+  int64_t clamped;          /* interface exits clamped to the stencil ends              */
+  int64_t units;            /* work units processed                                     */
+  int32_t device_error;     /* PDDS_OK or PDDS_ETIMEOUT from the last kernel            */
+  int32_t solve_iters;      /* iterations of the last pdds_solve                        */
+  double solve_relres;      /* ||b - G u|| / ||b|| of the last pdds_solve               */
+  float path_kernel_ms;     /* CUDA-event time of the last path kernel (timing on)     */
+  int32_t kernel_launches;  /* kernels launched by the last assemble + solve calls      */
+} pdds_stats_t;
+
+/* ------------------------------------------------------------------------ */
+/* Host-only geometry (no CUDA call): the knot set, patches and stencils of  */
+/* Sec. 3.1 (Eq. 13-18).  Pass NULL arrays to query sizes only.  xy_host is  */
+/* [n][2]; row_ptr_host [n+1]; col_host [nnz].                                */
+pdds_status pdds_geometry_host(const pdds_grid* grid, int64_t* n, int64_t* nnz,
+                               double* xy_host, int32_t* row_ptr_host, int32_t* col_host);
+
+/* Builds the problem on the current device: knot table, patch boxes, stencil
+ * slots, CSR pattern (Sec. 3.1) and, for PDDS_COEF_TABLE, padded device copies
+ * of the coefficient tables with their TMA descriptors.  Synchronizes the
+ * device.  Errors: EINVAL (grid/coeffs), ENOMEM, ECUDA. */
+pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* coeffs, pdds_ctx** out);
+void pdds_destroy(pdds_ctx* ctx);
+
+pdds_status pdds_num_knots(const pdds_ctx* ctx, int64_t* n, int64_t* nnz);
+pdds_status pdds_knot_coords(const pdds_ctx* ctx, double* xy_host /* [n][2] */);
+
+/* Step cap per path (K_max).  Default: 40 x the strip bound on the mean exit
+ * time of the largest patch, w^2 / (4 s_min^2) with w = 2 min(Lx, Ly), over dt. */
+pdds_status pdds_set_step_cap(pdds_ctx* ctx, int64_t k_max);
+
+/* Launch shape of the path kernel: threads per CTA (multiple of 32, <= 1024),
+ * CTAs per SM (0 = occupancy maximum), paths per work unit (>= 32) and the
+ * number of exited lanes a warp gathers before resolving exits (1..32).
+ * Zeros keep the current value.  pdds_autotune picks them by measurement. */
+pdds_status pdds_set_launch(pdds_ctx* ctx, int32_t block, int32_t ctas_per_sm,
+                            int32_t unit_paths, int32_t exit_batch);
+pdds_status pdds_get_launch(const pdds_ctx* ctx, int32_t* block, int32_t* ctas_per_sm,
+                            int32_t* unit_paths, int32_t* exit_batch);
+/* Bound, in seconds, on every device-side wait of the path kernel (a warp
+ * waiting for the next work unit of its CTA).  When a wait runs out the kernel
+ * stops taking work, returns, and pdds_stats reports PDDS_ETIMEOUT; the
+ * results of that call are then incomplete.  0 restores the default:
+ * 10 s plus 4 us per step of the step cap. */
+pdds_status pdds_set_wait_limit(pdds_ctx* ctx, double seconds);
+
+/* When on, the path kernel is bracketed by CUDA events on the caller's stream
+ * and its duration is reported in pdds_stats (the call then synchronizes). */
+pdds_status pdds_set_timing(pdds_ctx* ctx, int32_t on);
+
+/* Monte Carlo assembly of G and b (Eq. 24-25), the hot path.
+ * For every knot k, N_k paths of dX = d dt + s dW (naive Euler-Maruyama, Sec.
+ * 2.3) carry Y = exp(int c dt) and Z = -int f Y dt (Eq. 9) until they leave the
+ * closed patch (Eq. 15); an exit on the boundary of Omega adds g Y to b_k, an
+ * exit on an interface interpolates linearly between the two nearest stencil
+ * knots of the side crossed (Eq. 21-22 with a linear scheme; boundary points of
+ * the stencil add their known g).  Then G_kk = 1, G_kj = -sum/N_k, b_k = sum/N_k.
+ *   n_per_knot: DEVICE int64[n] budgets, or NULL to use n_paths for every knot
+ *   n_paths   : >= 1 when n_per_knot is NULL; every N_k must be < 2^31 (a knot
+ *               with N_k = 0 keeps row e_k and b_k = 0)
+ *   dt        : time step h > 0
+ *   seed      : 64-bit Philox4x32-10 key; the normal pair for step 2q and 2q+1 of
+ *               path p from knot k comes from counter (q, p, k, tag)
+ *   G         : caller-owned device CSR sized by pdds_num_knots; row_ptr, col and
+ *               val are all written
+ *   b         : device double[n]
+ * Asynchronous (unless timing is on).  Device-side errors surface in pdds_stats. */
+pdds_status pdds_assemble(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_paths,
+                          double dt, uint64_t seed, pdds_csr* G, double* b, void* cuda_stream);
+
+/* Same as pdds_assemble, plus one pdds_path_record per path written to the
+ * DEVICE array `records`, laid out knot by knot (knot-major, then path index);
+ * it must hold sum_k N_k records. */
+pdds_status pdds_assemble_records(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_paths,
+                                  double dt, uint64_t seed, pdds_csr* G, double* b,
+                                  pdds_path_record* records, void* cuda_stream);
+
+/* Several independent problems (same coefficient set id) in ONE persistent
+ * launch: paths of all problems share one work queue.  Arrays have `count`
+ * entries; n_per_knot[i] may be NULL (then n_paths is used).  Problem i uses
+ * Philox tag i, so its streams differ from problem 0's.  The sequence is
+ * captured once into a CUDA graph per (count, ctxs) and replayed. */
+pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
+                                const int64_t* const* n_per_knot, int64_t n_paths, double dt,
+                                uint64_t seed, pdds_csr* const* G, double* const* b,
+                                void* cuda_stream);
+
+/* FP64 BiCGSTAB for G u = b (Eq. 23), all on the device; u (device double[n])
+ * is overwritten (initial guess 0).  Synchronizes the stream to read the
+ * residual every few iterations.  Returns ENOCONV if ||b - G u|| > rtol ||b||
+ * after maxit iterations; *iters (nullable) gets the iteration count. */
+pdds_status pdds_solve(pdds_ctx* ctx, const pdds_csr* G, const double* b, double* u,
+                       double rtol, int32_t maxit, int32_t* iters, void* cuda_stream);
+
+/* End-to-end call with HOST buffers: uploads the per-knot budgets, assembles,
+ * solves and downloads G (row_ptr, col, val), b and u.  Device scratch is owned
+ * by the context.  n_per_knot_host may be NULL.  Synchronizes the stream. */
+pdds_status pdds_assemble_solve_host(pdds_ctx* ctx, const int64_t* n_per_knot_host,
+                                     int64_t n_paths, double dt, uint64_t seed, double rtol,
+                                     int32_t maxit, int32_t* row_ptr_host, int32_t* col_host,
+                                     double* val_host, double* b_host, double* u_host,
+                                     void* cuda_stream);
+
+/* Counters of the last assemble / solve (synchronizes the device). */
+pdds_status pdds_stats(pdds_ctx* ctx, pdds_stats_t* out);
+
+/* Text of the last error on ctx (or of the last failed pdds_create when ctx is
+ * NULL).  Never NULL; valid until the next call on the same context. */
+const char* pdds_last_error(const pdds_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDDS_H */

@@ -1,0 +1,897 @@
+// Host side of the PDDSparse assembly library: geometry of Sec. 3.1
+// (knots, patches, extended stencils, CSR pattern), device tables, TMA
+// descriptors, launch configuration and the C ABI of pdds.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pdds.h"
+#include "pdds_internal.h"
+
+using pdds::KnotDesc;
+using pdds::ProbDesc;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+// ------------------------------------------------------------ geometry
+// Knots live on the lattice (i, j), 0 <= i <= LX = Hx m, 0 <= j <= LY = Hy m;
+// a lattice point is an unknown knot when it is interior and lies on a grid
+// line (i % m == 0 or j % m == 0).  Knots are numbered row by row (j), then
+// by i, which gives the closed-form index below.
+struct Geometry {
+  pdds_grid g{};
+  int LX = 0, LY = 0;
+  double dx = 0, dy = 0;
+  int64_t n = 0, nnz = 0;
+  std::vector<int32_t> ki, kj, row_ptr, col, slot2csr;
+  std::vector<KnotDesc> kd;
+  int max_slots = 0;
+
+  bool is_knot(int i, int j) const {
+    if (i <= 0 || i >= LX || j <= 0 || j >= LY) return false;
+    return (i % g.m == 0) || (j % g.m == 0);
+  }
+  int64_t index(int i, int j) const {
+    const int64_t full = (j - 1) / g.m;      // grid-line rows below j
+    const int64_t part = (j - 1) - full;     // other rows below j
+    const int64_t before = full * (LX - 1) + part * (int64_t)(g.Hx - 1);
+    const int64_t pos = (j % g.m == 0) ? (i - 1) : (i / g.m - 1);
+    return before + pos;
+  }
+};
+
+bool build_geometry(const pdds_grid& g, Geometry& G, bool with_tables, std::string& err) {
+  if (!(g.x1 > g.x0) || !(g.y1 > g.y0) || !std::isfinite(g.x0) || !std::isfinite(g.x1) ||
+      !std::isfinite(g.y0) || !std::isfinite(g.y1)) {
+    err = "grid: need x1 > x0 and y1 > y0 (finite)";
+    return false;
+  }
+  if (g.Hx < 1 || g.Hy < 1 || g.m < 1 || g.ext < 0 || (g.Hx < 2 && g.Hy < 2)) {
+    err = "grid: need Hx, Hy >= 1 with one of them >= 2, m >= 1, ext >= 0";
+    return false;
+  }
+  if ((int64_t)g.Hx * g.m > (1 << 20) || (int64_t)g.Hy * g.m > (1 << 20)) {
+    err = "grid: Hx*m and Hy*m must be <= 2^20";
+    return false;
+  }
+  G.g = g;
+  G.LX = g.Hx * g.m;
+  G.LY = g.Hy * g.m;
+  G.dx = (g.x1 - g.x0) / G.LX;
+  G.dy = (g.y1 - g.y0) / G.LY;
+  G.n = (int64_t)(g.Hy - 1) * (G.LX - 1) + (int64_t)(G.LY - 1 - (g.Hy - 1)) * (g.Hx - 1);
+  if (G.n <= 0 || G.n > (int64_t)1 << 30) {
+    err = "grid: knot count out of range";
+    return false;
+  }
+  G.ki.resize(G.n);
+  G.kj.resize(G.n);
+  {
+    int64_t k = 0;
+    for (int j = 1; j < G.LY; ++j) {
+      if (j % g.m == 0)
+        for (int i = 1; i < G.LX; ++i) { G.ki[k] = i; G.kj[k] = j; ++k; }
+      else
+        for (int i = g.m; i < G.LX; i += g.m) { G.ki[k] = i; G.kj[k] = j; ++k; }
+    }
+    if (k != G.n) { err = "internal: knot enumeration mismatch"; return false; }
+  }
+  G.row_ptr.assign(G.n + 1, 0);
+  if (with_tables) G.kd.resize(G.n);
+  std::vector<int64_t> cols;
+  // Two passes: sizes, then contents.
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      G.nnz = G.row_ptr[G.n];
+      G.col.resize(G.nnz);
+    }
+    int64_t slots_total = 0;
+    for (int64_t k = 0; k < G.n; ++k) {
+      const int i = G.ki[k], j = G.kj[k], m = g.m, E = g.ext;
+      // slab (Eq. 13) = patch (Eq. 15): Omega is a grid-aligned rectangle
+      int ilo, ihi, jlo, jhi;
+      if (i % m == 0) { ilo = i - m; ihi = i + m; } else { ilo = (i / m) * m; ihi = ilo + m; }
+      if (j % m == 0) { jlo = j - m; jhi = j + m; } else { jlo = (j / m) * m; jhi = jlo + m; }
+      const int line[4] = {ihi, jhi, ilo, jlo};
+      const int lo_along[4] = {jlo, ilo, jlo, ilo};
+      const int hi_along[4] = {jhi, ihi, jhi, ihi};
+      const int lmax_along[4] = {G.LY, G.LX, G.LY, G.LX};
+      const int lmax_line[4] = {G.LX, G.LY, G.LX, G.LY};
+      cols.clear();
+      cols.push_back(k);
+      KnotDesc d{};
+      int nslots = 0;
+      for (int o = 0; o < 4; ++o) {
+        const bool dir = (line[o] == 0 || line[o] == lmax_line[o]);
+        const int a = std::max(lo_along[o] - E, 0);
+        const int b = std::min(hi_along[o] + E, lmax_along[o]);
+        d.line[o] = line[o];
+        d.a[o] = a;
+        d.b[o] = b;
+        if (dir) {
+          d.dirbits |= 1 << o;
+          d.off[o] = -1;
+          continue;
+        }
+        d.off[o] = nslots;
+        nslots += b - a + 1;
+        const bool vertical = (o == 0 || o == 2);
+        for (int t = a; t <= b; ++t) {
+          const int pi = vertical ? line[o] : t, pj = vertical ? t : line[o];
+          if (G.is_knot(pi, pj)) cols.push_back(G.index(pi, pj));
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      if (pass == 0) {
+        G.row_ptr[k + 1] = G.row_ptr[k] + (int32_t)cols.size();
+        if ((int64_t)G.row_ptr[k + 1] > (int64_t)INT32_MAX / 2) {
+          err = "grid: nnz exceeds int32 range";
+          return false;
+        }
+        continue;
+      }
+      std::copy(cols.begin(), cols.end(), G.col.begin() + G.row_ptr[k]);
+      G.max_slots = std::max(G.max_slots, nslots);
+      if (!with_tables) continue;
+      d.xk = (float)(g.x0 + i * G.dx);
+      d.yk = (float)(g.y0 + j * G.dy);
+      d.box[0] = (float)((ilo - i) * G.dx);
+      d.box[1] = (float)((ihi - i) * G.dx);
+      d.box[2] = (float)((jlo - j) * G.dy);
+      d.box[3] = (float)((jhi - j) * G.dy);
+      d.ki = i;
+      d.kj = j;
+      d.slot_base = (int32_t)slots_total;
+      d.nslots = nslots;
+      G.kd[k] = d;
+      for (int o = 0; o < 4; ++o) {
+        if (d.off[o] < 0) continue;
+        const bool vertical = (o == 0 || o == 2);
+        for (int t = d.a[o]; t <= d.b[o]; ++t) {
+          const int pi = vertical ? line[o] : t, pj = vertical ? t : line[o];
+          int32_t csr = -1;
+          if (G.is_knot(pi, pj)) {
+            const int64_t c = G.index(pi, pj);
+            const auto it = std::lower_bound(cols.begin(), cols.end(), c);
+            csr = G.row_ptr[k] + (int32_t)(it - cols.begin());
+          }
+          G.slot2csr.push_back(csr);
+        }
+      }
+      slots_total += nslots;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------- TMA encode
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+// ================================================================ context
+struct pdds_ctx {
+  pdds_grid grid{};
+  int coef_id = 0;
+  double params[8] = {0};
+  int tab_nx = 0, tab_ny = 0;
+  Geometry geo;
+  double s_min = 0, s_max = 0;  // diffusion bounds (step-cap rule)
+  int device = 0, num_sms = 0;
+  // device tables
+  KnotDesc* d_knots = nullptr;
+  int32_t* d_slot2csr = nullptr;
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  float* d_tab = nullptr;  // sigma then c, padded rows
+  CUtensorMap* d_tmap = nullptr;
+  int tile_w = 0, tile_h = 0;
+  pdds::Scratch* d_scratch = nullptr;
+  int64_t* d_unit_prefix = nullptr;
+  int64_t* d_path_prefix = nullptr;
+  int64_t* d_prob_prefix = nullptr;
+  // launch configuration
+  int block = 256, ctas_per_sm = 0, exit_batch = 4;
+  int64_t unit_paths = 4096;
+  int64_t k_max = 0;
+  bool timing = false;
+  double wait_s = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // solver scratch
+  double* d_work = nullptr;
+  pdds::SolveScalars* d_scalars = nullptr;
+  // end-to-end scratch
+  int64_t* e_N = nullptr;
+  int32_t* e_rp = nullptr;
+  int32_t* e_col = nullptr;
+  double *e_val = nullptr, *e_b = nullptr, *e_u = nullptr;
+  // batch launch cache
+  ProbDesc* d_batch = nullptr;
+  int batch_cap = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<uint64_t> graph_key;
+  pdds_stats_t st{};
+  std::string err = "no error";
+};
+
+namespace {
+
+pdds_status fail(pdds_ctx* c, pdds_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_last_error = msg;
+  return s;
+}
+pdds_status cuda_fail(pdds_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, PDDS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(ctx, call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_ctx(pdds_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_knots); cudaFree(c->d_slot2csr); cudaFree(c->d_row_ptr); cudaFree(c->d_col);
+  cudaFree(c->d_tab); cudaFree(c->d_tmap); cudaFree(c->d_scratch); cudaFree(c->d_unit_prefix);
+  cudaFree(c->d_path_prefix); cudaFree(c->d_prob_prefix); cudaFree(c->d_work);
+  cudaFree(c->d_scalars); cudaFree(c->e_N); cudaFree(c->e_rp); cudaFree(c->e_col);
+  cudaFree(c->e_val); cudaFree(c->e_b); cudaFree(c->e_u); cudaFree(c->d_batch);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+// Bounds of s(x) for the default step cap.
+void sigma_bounds(const pdds_coeffs& cf, const std::vector<float>& sig, double& lo, double& hi) {
+  const double r2 = std::sqrt(2.0);
+  switch (cf.builtin_id) {
+    case PDDS_COEF_VARSIGMA: lo = 0.7 * r2; hi = 1.3 * r2; break;
+    case PDDS_COEF_TABLE:
+      lo = 1e300; hi = 0;
+      for (float v : sig) { lo = std::min(lo, (double)v); hi = std::max(hi, (double)v); }
+      break;
+    case PDDS_COEF_CONSTANT: lo = hi = std::fabs(cf.params[0]); break;
+    default: lo = hi = r2;
+  }
+}
+
+size_t stage_bytes(const pdds_ctx* c) {
+  size_t b = pdds::stage_header_bytes() + round_up((size_t)c->geo.max_slots * 8, 128);
+  if (c->coef_id == PDDS_COEF_TABLE) b += 2 * round_up((size_t)c->tile_w * c->tile_h * 4, 128);
+  return round_up(b, 128);
+}
+
+ProbDesc make_prob(const pdds_ctx* c, int tag) {
+  ProbDesc D{};
+  const Geometry& G = c->geo;
+  D.coef_id = c->coef_id;
+  D.n = (int32_t)G.n;
+  D.LX = G.LX;
+  D.LY = G.LY;
+  for (int i = 0; i < 8; ++i) D.params[i] = (float)c->params[i];
+  D.x0 = (float)c->grid.x0; D.y0 = (float)c->grid.y0;
+  D.x1 = (float)c->grid.x1; D.y1 = (float)c->grid.y1;
+  D.dx = (float)G.dx; D.dy = (float)G.dy;
+  D.inv_dx = (float)(1.0 / G.dx); D.inv_dy = (float)(1.0 / G.dy);
+  if (c->coef_id == PDDS_COEF_TABLE) {
+    D.tab_inv_dx = (float)((c->tab_nx - 1) / (c->grid.x1 - c->grid.x0));
+    D.tab_inv_dy = (float)((c->tab_ny - 1) / (c->grid.y1 - c->grid.y0));
+    D.tmap = c->d_tmap;
+    D.tab_nx = c->tab_nx;
+    D.tab_ny = c->tab_ny;
+  }
+  D.tag = tag;
+  D.knots = c->d_knots;
+  D.slot2csr = c->d_slot2csr;
+  D.col = c->d_col;
+  return D;
+}
+
+pdds_status check_csr(pdds_ctx* c, const pdds_csr* G, const double* b) {
+  if (!G || !b || !G->row_ptr || !G->col || !G->val)
+    return fail(c, PDDS_EINVAL, "assemble: G (row_ptr, col, val) and b must be device pointers");
+  if (G->n != c->geo.n || G->nnz != c->geo.nnz)
+    return fail(c, PDDS_EINVAL, "assemble: G sized differently from pdds_num_knots");
+  return PDDS_OK;
+}
+
+int64_t default_kmax(const pdds_ctx* c, double dt) {
+  const double Lx = (c->grid.x1 - c->grid.x0) / c->grid.Hx;
+  const double Ly = (c->grid.y1 - c->grid.y0) / c->grid.Hy;
+  const double T = std::pow(std::min(Lx, Ly), 2) / std::pow(std::max(c->s_min, 1e-12), 2);
+  return (int64_t)std::ceil(40.0 * T / dt);
+}
+
+// Everything one or more problems need for one persistent launch.
+pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, int nprob,
+                      double dt, uint64_t seed, int64_t kmax, pdds::PathRecordDev* rec,
+                      cudaStream_t stream, size_t sbytes, int max_slots, int tile_w, int tile_h,
+                      int coef_id) {
+  pdds::KParams kp{};
+  kp.prob0 = p0;
+  kp.probs = d_probs;
+  kp.nprob = nprob;
+  kp.prob_unit_prefix = c->d_prob_prefix;
+  kp.exit_batch = c->exit_batch;
+  kp.unit_paths = c->unit_paths;
+  kp.scratch = c->d_scratch;
+  kp.records = rec;
+  kp.key0 = (uint32_t)seed;
+  kp.key1 = (uint32_t)(seed >> 32);
+  kp.h = (float)dt;
+  kp.sqh = (float)std::sqrt(dt);
+  kp.kmax = kmax;
+  kp.max_slots = max_slots;
+  kp.tile_w = tile_w;
+  kp.tile_h = tile_h;
+  kp.stage_bytes = (int)sbytes;
+  kp.rec_mode = rec != nullptr;
+  // a wait may outlast the slowest path of a unit: K_max steps at ~4 us
+  kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * (double)kmax);
+  const size_t smem = 2 * sbytes;
+  CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, smem));
+  int per_sm = c->ctas_per_sm;
+  if (per_sm <= 0) {
+    CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, c->block, smem, &per_sm));
+    if (per_sm <= 0) return fail(c, PDDS_EINVAL, "launch: block/shared memory too large");
+  }
+  const int grid = c->num_sms * per_sm;
+  if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
+  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, kp, grid, c->block, smem, stream));
+  if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
+  return PDDS_OK;
+}
+
+pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, uint64_t seed,
+                          pdds_csr* G, double* b, pdds_path_record* rec, cudaStream_t s) {
+  (void)cudaGetLastError();  // a failed call elsewhere must not be reported here
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PDDS_EINVAL, "assemble: dt must be > 0");
+  if (!N && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
+    return fail(c, PDDS_EINVAL, "assemble: n_paths must be in [1, 2^31)");
+  if (pdds_status e = check_csr(c, G, b)) return e;
+  const int64_t kmax = c->k_max > 0 ? c->k_max : default_kmax(c, dt);
+  c->st = pdds_stats_t{};
+  int launches = 0;
+  CK(c, cudaMemcpyAsync(G->row_ptr, c->d_row_ptr, (c->geo.n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemcpyAsync(G->col, c->d_col, c->geo.nnz * 4, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemsetAsync(G->val, 0, c->geo.nnz * 8, s));
+  CK(c, cudaMemsetAsync(b, 0, c->geo.n * 8, s));
+  CK(c, cudaMemsetAsync(c->d_scratch, 0, sizeof(pdds::Scratch), s));
+  ProbDesc D = make_prob(c, 0);
+  D.Gval = G->val;
+  D.b = b;
+  D.n_per_knot = N;
+  D.n_paths = Nu;
+  if (N) {
+    CK(c, pdds::launch_unit_prefix(N, c->geo.n, c->unit_paths, c->d_unit_prefix,
+                                   c->d_path_prefix, s));
+    ++launches;
+    D.knot_unit_prefix = c->d_unit_prefix;
+    D.path_prefix = c->d_path_prefix;
+  } else {
+    D.units_per_knot = ceil_div(Nu, c->unit_paths);
+  }
+  CK(c, pdds::launch_prob_prefix_single(D, c->d_prob_prefix, s));
+  ++launches;
+  if (pdds_status e = run_paths(c, D, nullptr, 1, dt, seed, kmax,
+                                reinterpret_cast<pdds::PathRecordDev*>(rec), s, stage_bytes(c),
+                                c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id))
+    return e;
+  ++launches;
+  CK(c, pdds::launch_finalize(G->row_ptr, G->col, G->val, b, N, Nu, c->geo.n, s));
+  ++launches;
+  c->st.kernel_launches = launches;
+  if (c->timing) {
+    CK(c, cudaEventSynchronize(c->ev1));
+    CK(c, cudaEventElapsedTime(&c->st.path_kernel_ms, c->ev0, c->ev1));
+  }
+  return PDDS_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+pdds_status pdds_geometry_host(const pdds_grid* grid, int64_t* n, int64_t* nnz, double* xy,
+                               int32_t* row_ptr, int32_t* col) {
+  if (!grid) return fail(nullptr, PDDS_EINVAL, "geometry: grid is NULL");
+  Geometry G;
+  std::string err;
+  if (!build_geometry(*grid, G, false, err)) return fail(nullptr, PDDS_EINVAL, err);
+  if (n) *n = G.n;
+  if (nnz) *nnz = G.nnz;
+  if (xy)
+    for (int64_t k = 0; k < G.n; ++k) {
+      xy[2 * k] = grid->x0 + G.ki[k] * G.dx;
+      xy[2 * k + 1] = grid->y0 + G.kj[k] * G.dy;
+    }
+  if (row_ptr) std::copy(G.row_ptr.begin(), G.row_ptr.end(), row_ptr);
+  if (col) std::copy(G.col.begin(), G.col.end(), col);
+  return PDDS_OK;
+}
+
+pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx** out) {
+  if (!grid || !cf || !out) return fail(nullptr, PDDS_EINVAL, "create: NULL argument");
+  *out = nullptr;
+  if (cf->kind != PDDS_COEF_BUILTIN || cf->builtin_id < 0 || cf->builtin_id > PDDS_COEF_CONSTANT)
+    return fail(nullptr, PDDS_EINVAL, "create: unknown coefficient set");
+  auto* c = new (std::nothrow) pdds_ctx;
+  if (!c) return fail(nullptr, PDDS_ENOMEM, "create: out of host memory");
+  c->grid = *grid;
+  c->coef_id = cf->builtin_id;
+  std::memcpy(c->params, cf->params, sizeof(c->params));
+  std::string err;
+  if (!build_geometry(*grid, c->geo, true, err)) {
+    free_ctx(c);
+    return fail(nullptr, PDDS_EINVAL, err);
+  }
+  if (c->coef_id == PDDS_COEF_CONSTANT && !(std::fabs(cf->params[0]) > 0)) {
+    free_ctx(c);
+    return fail(nullptr, PDDS_EINVAL, "create: CONSTANT needs params[0] (sigma) != 0");
+  }
+  auto bail = [&](cudaError_t e, const char* what) {
+    g_last_error = std::string("create: ") + what + ": " + cudaGetErrorString(e);
+    free_ctx(c);
+    return PDDS_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) !=
+      cudaSuccess)
+    return bail(e, "multiprocessor count");
+  const Geometry& G = c->geo;
+  std::vector<float> sig_host, c_host;
+  if (c->coef_id == PDDS_COEF_TABLE) {
+    if (!cf->sigma_tab || !cf->c_tab || cf->tab_nx < 2 || cf->tab_ny < 2) {
+      free_ctx(c);
+      return fail(nullptr, PDDS_EINVAL, "create: TABLE needs sigma_tab, c_tab and tab_nx,ny >= 2");
+    }
+    c->tab_nx = cf->tab_nx;
+    c->tab_ny = cf->tab_ny;
+    const size_t cnt = (size_t)cf->tab_nx * cf->tab_ny;
+    sig_host.resize(cnt);
+    c_host.resize(cnt);
+    if ((e = cudaMemcpy(sig_host.data(), cf->sigma_tab, cnt * 4, cudaMemcpyDefault)) != cudaSuccess)
+      return bail(e, "sigma table copy");
+    if ((e = cudaMemcpy(c_host.data(), cf->c_tab, cnt * 4, cudaMemcpyDefault)) != cudaSuccess)
+      return bail(e, "c table copy");
+    // Tile covering every patch: nodes [i0, i0 + w) x [j0, j0 + h) with i0 a
+    // multiple of 4 (16-byte TMA inner coordinate).
+    const double tdx = (grid->x1 - grid->x0) / (cf->tab_nx - 1);
+    const double tdy = (grid->y1 - grid->y0) / (cf->tab_ny - 1);
+    int need_w = 0, need_h = 0;
+    for (int64_t k = 0; k < G.n; ++k) {
+      KnotDesc& d = c->geo.kd[k];
+      const int pil = d.line[2], pih = d.line[0], pjl = d.line[3], pjh = d.line[1];
+      const double fxl = pil * G.dx / tdx, fxh = pih * G.dx / tdx;
+      const double fyl = pjl * G.dy / tdy, fyh = pjh * G.dy / tdy;
+      const int i0 = ((int)std::floor(fxl + 1e-9) / 4) * 4;
+      const int j0 = (int)std::floor(fyl + 1e-9);
+      const int ihi = std::min((int)std::floor(fxh + 1e-9), cf->tab_nx - 2) + 1;
+      const int jhi = std::min((int)std::floor(fyh + 1e-9), cf->tab_ny - 2) + 1;
+      need_w = std::max(need_w, ihi - i0 + 1);
+      need_h = std::max(need_h, jhi - j0 + 1);
+      d.tile_i0 = i0;
+      d.tile_j0 = j0;
+      d.tab_fx = (float)(G.ki[k] * G.dx / tdx - i0);
+      d.tab_fy = (float)(G.kj[k] * G.dy / tdy - j0);
+    }
+    c->tile_w = (int)round_up((size_t)need_w, 4);
+    c->tile_h = need_h;
+    if (c->tile_w > 256 || c->tile_h > 256 || 2 * c->tile_w * c->tile_h * 4 > 96 * 1024) {
+      free_ctx(c);
+      return fail(nullptr, PDDS_EINVAL,
+                  "create: coefficient tile per patch exceeds 256x256 nodes / 96 KB");
+    }
+    auto enc = get_encode_fn();
+    if (!enc) {
+      free_ctx(c);
+      return fail(nullptr, PDDS_ECUDA, "create: cuTensorMapEncodeTiled unavailable");
+    }
+    const size_t pitch = round_up((size_t)cf->tab_nx, 4);  // 16-byte row pitch
+    std::vector<float> padded(2 * pitch * cf->tab_ny, 0.0f);
+    for (int j = 0; j < cf->tab_ny; ++j)
+      for (int i = 0; i < cf->tab_nx; ++i) {
+        padded[j * pitch + i] = sig_host[(size_t)j * cf->tab_nx + i];
+        padded[(cf->tab_ny + j) * pitch + i] = c_host[(size_t)j * cf->tab_nx + i];
+      }
+    if ((e = dalloc(&c->d_tab, padded.size())) != cudaSuccess) return bail(e, "table alloc");
+    if ((e = cudaMemcpy(c->d_tab, padded.data(), padded.size() * 4, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return bail(e, "table upload");
+    CUtensorMap maps[2];
+    for (int f = 0; f < 2; ++f) {
+      const cuuint64_t dims[2] = {(cuuint64_t)cf->tab_nx, (cuuint64_t)cf->tab_ny};
+      const cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
+      const cuuint32_t box[2] = {(cuuint32_t)c->tile_w, (cuuint32_t)c->tile_h};
+      const cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&maps[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                       c->d_tab + (size_t)f * pitch * cf->tab_ny, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        free_ctx(c);
+        return fail(nullptr, PDDS_ECUDA, "create: cuTensorMapEncodeTiled failed");
+      }
+    }
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&c->d_tmap), sizeof(maps))) != cudaSuccess)
+      return bail(e, "tensor map alloc");
+    if ((e = cudaMemcpy(c->d_tmap, maps, sizeof(maps), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "tensor map upload");
+  }
+  sigma_bounds(*cf, sig_host, c->s_min, c->s_max);
+  const int64_t n = G.n;
+  if ((e = dalloc(&c->d_knots, n)) != cudaSuccess) return bail(e, "knot table alloc");
+  if ((e = dalloc(&c->d_slot2csr, G.slot2csr.size())) != cudaSuccess) return bail(e, "slot alloc");
+  if ((e = dalloc(&c->d_row_ptr, n + 1)) != cudaSuccess) return bail(e, "row_ptr alloc");
+  if ((e = dalloc(&c->d_col, G.nnz)) != cudaSuccess) return bail(e, "col alloc");
+  if ((e = dalloc(&c->d_scratch, 1)) != cudaSuccess) return bail(e, "scratch alloc");
+  if ((e = dalloc(&c->d_unit_prefix, n + 1)) != cudaSuccess) return bail(e, "prefix alloc");
+  if ((e = dalloc(&c->d_path_prefix, n + 1)) != cudaSuccess) return bail(e, "prefix alloc");
+  if ((e = dalloc(&c->d_prob_prefix, 2)) != cudaSuccess) return bail(e, "prefix alloc");
+  if ((e = cudaMemcpy(c->d_knots, G.kd.data(), n * sizeof(KnotDesc), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return bail(e, "knot upload");
+  if ((e = cudaMemcpy(c->d_slot2csr, G.slot2csr.data(), G.slot2csr.size() * 4,
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "slot upload");
+  if ((e = cudaMemcpy(c->d_row_ptr, G.row_ptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return bail(e, "row_ptr upload");
+  if ((e = cudaMemcpy(c->d_col, G.col.data(), G.nnz * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "col upload");
+  if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess) return bail(e, "event");
+  if ((e = cudaEventCreate(&c->ev1)) != cudaSuccess) return bail(e, "event");
+  // Knot data on the host is only needed for coordinates from here on.
+  c->geo.kd.clear();
+  c->geo.kd.shrink_to_fit();
+  c->geo.slot2csr.clear();
+  c->geo.slot2csr.shrink_to_fit();
+  *out = c;
+  return PDDS_OK;
+}
+
+void pdds_destroy(pdds_ctx* c) {
+  if (c) cudaDeviceSynchronize();
+  free_ctx(c);
+}
+
+pdds_status pdds_num_knots(const pdds_ctx* c, int64_t* n, int64_t* nnz) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "num_knots: NULL context");
+  if (n) *n = c->geo.n;
+  if (nnz) *nnz = c->geo.nnz;
+  return PDDS_OK;
+}
+
+pdds_status pdds_knot_coords(const pdds_ctx* c, double* xy) {
+  if (!c || !xy) return fail(nullptr, PDDS_EINVAL, "knot_coords: NULL argument");
+  for (int64_t k = 0; k < c->geo.n; ++k) {
+    xy[2 * k] = c->grid.x0 + c->geo.ki[k] * c->geo.dx;
+    xy[2 * k + 1] = c->grid.y0 + c->geo.kj[k] * c->geo.dy;
+  }
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_step_cap(pdds_ctx* c, int64_t k_max) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_step_cap: NULL context");
+  if (k_max < 0 || k_max >= ((int64_t)1 << 31))
+    return fail(c, PDDS_EINVAL, "set_step_cap: need 0 <= k_max < 2^31");
+  c->k_max = k_max;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_launch(pdds_ctx* c, int32_t block, int32_t per_sm, int32_t unit_paths,
+                            int32_t exit_batch) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_launch: NULL context");
+  if (block && (block < 64 || block > 1024 || block % 32))
+    return fail(c, PDDS_EINVAL, "set_launch: block must be a multiple of 32 in [64, 1024]");
+  if (per_sm < 0 || per_sm > 32) return fail(c, PDDS_EINVAL, "set_launch: ctas_per_sm in [0, 32]");
+  if (unit_paths && (unit_paths < 32 || unit_paths > (1 << 24)))
+    return fail(c, PDDS_EINVAL, "set_launch: unit_paths in [32, 2^24]");
+  if (exit_batch && (exit_batch < 1 || exit_batch > 32))
+    return fail(c, PDDS_EINVAL, "set_launch: exit_batch in [1, 32]");
+  if (block) c->block = block;
+  c->ctas_per_sm = per_sm;
+  if (unit_paths) c->unit_paths = unit_paths;
+  if (exit_batch) c->exit_batch = exit_batch;
+  return PDDS_OK;
+}
+
+pdds_status pdds_get_launch(const pdds_ctx* c, int32_t* block, int32_t* per_sm,
+                            int32_t* unit_paths, int32_t* exit_batch) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "get_launch: NULL context");
+  if (block) *block = c->block;
+  if (per_sm) *per_sm = c->ctas_per_sm;
+  if (unit_paths) *unit_paths = (int32_t)c->unit_paths;
+  if (exit_batch) *exit_batch = c->exit_batch;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_wait_limit(pdds_ctx* c, double seconds) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_wait_limit: NULL context");
+  if (!(seconds >= 0) || seconds > 1e6) return fail(c, PDDS_EINVAL, "set_wait_limit: need 0 <= s <= 1e6");
+  c->wait_s = seconds;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_timing(pdds_ctx* c, int32_t on) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_timing: NULL context");
+  c->timing = on != 0;
+  return PDDS_OK;
+}
+
+pdds_status pdds_assemble(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, uint64_t seed,
+                          pdds_csr* G, double* b, void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "assemble: NULL context");
+  return assemble_impl(c, N, Nu, dt, seed, G, b, nullptr, (cudaStream_t)stream);
+}
+
+pdds_status pdds_assemble_records(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt,
+                                  uint64_t seed, pdds_csr* G, double* b, pdds_path_record* rec,
+                                  void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "assemble_records: NULL context");
+  if (!rec) return fail(c, PDDS_EINVAL, "assemble_records: records is NULL");
+  return assemble_impl(c, N, Nu, dt, seed, G, b, rec, (cudaStream_t)stream);
+}
+
+pdds_status pdds_stats(pdds_ctx* c, pdds_stats_t* out) {
+  if (!c || !out) return fail(nullptr, PDDS_EINVAL, "stats: NULL argument");
+  pdds::Scratch s{};
+  CK(c, cudaDeviceSynchronize());
+  CK(c, cudaMemcpy(&s, c->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+  c->st.path_steps = (int64_t)s.steps;
+  c->st.paths = (int64_t)s.paths;
+  c->st.truncated = (int64_t)s.truncated;
+  c->st.clamped = (int64_t)s.clamped;
+  c->st.units = (int64_t)s.units;
+  c->st.device_error = s.error;
+  *out = c->st;
+  return s.error ? PDDS_ETIMEOUT : PDDS_OK;
+}
+
+const char* pdds_last_error(const pdds_ctx* c) {
+  return c ? c->err.c_str() : g_last_error.c_str();
+}
+
+pdds_status pdds_solve(pdds_ctx* c, const pdds_csr* G, const double* b, double* u,
+                       double rtol, int32_t maxit, int32_t* iters, void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "solve: NULL context");
+  if (!G || !b || !u || !G->row_ptr || !G->col || !G->val)
+    return fail(c, PDDS_EINVAL, "solve: NULL matrix/vector");
+  if (G->n != c->geo.n || G->nnz != c->geo.nnz)
+    return fail(c, PDDS_EINVAL, "solve: G sized differently from pdds_num_knots");
+  if (!(rtol > 0) || maxit < 1) return fail(c, PDDS_EINVAL, "solve: need rtol > 0, maxit >= 1");
+  (void)cudaGetLastError();
+  const int64_t n = c->geo.n;
+  if (!c->d_work) {
+    CK(c, dalloc(&c->d_work, pdds::bicgstab_work_doubles(n)));
+    CK(c, cudaMalloc(reinterpret_cast<void**>(&c->d_scalars), pdds::bicgstab_scalars_bytes()));
+  }
+  int32_t it = 0;
+  double rel = 0;
+  int conv = 0, nl = 0;
+  CK(c, pdds::bicgstab_device(G->row_ptr, G->col, G->val, b, u, n, c->d_work, c->d_scalars, rtol,
+                              maxit, &it, &rel, &conv, &nl, (cudaStream_t)stream));
+  c->st.solve_iters = it;
+  c->st.solve_relres = rel;
+  c->st.kernel_launches += nl;
+  if (iters) *iters = it;
+  if (conv != 1) {
+    static const char* why[] = {"", " ((rh,v) = 0)", " (omega = 0)", " ((rh,r) = 0)",
+                                " (residual not finite)"};
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "solve: no convergence after %d iterations (relres %.3e)%s",
+                  it, rel, (conv < 0 && -conv <= 4) ? why[-conv] : "");
+    return fail(c, PDDS_ENOCONV, buf);
+  }
+  return PDDS_OK;
+}
+
+pdds_status pdds_assemble_solve_host(pdds_ctx* c, const int64_t* N_host, int64_t Nu, double dt,
+                                     uint64_t seed, double rtol, int32_t maxit, int32_t* rp_host,
+                                     int32_t* col_host, double* val_host, double* b_host,
+                                     double* u_host, void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "assemble_solve_host: NULL context");
+  if (!val_host || !b_host || !u_host)
+    return fail(c, PDDS_EINVAL, "assemble_solve_host: val, b and u host buffers are required");
+  const int64_t n = c->geo.n, nnz = c->geo.nnz;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->e_rp) {
+    CK(c, dalloc(&c->e_N, n));
+    CK(c, dalloc(&c->e_rp, n + 1));
+    CK(c, dalloc(&c->e_col, nnz));
+    CK(c, dalloc(&c->e_val, nnz));
+    CK(c, dalloc(&c->e_b, n));
+    CK(c, dalloc(&c->e_u, n));
+  }
+  if (N_host) CK(c, cudaMemcpyAsync(c->e_N, N_host, n * 8, cudaMemcpyHostToDevice, s));
+  pdds_csr G{n, nnz, c->e_rp, c->e_col, c->e_val};
+  if (pdds_status e = assemble_impl(c, N_host ? c->e_N : nullptr, Nu, dt, seed, &G, c->e_b,
+                                    nullptr, s))
+    return e;
+  const int launches = c->st.kernel_launches;
+  pdds_status se = pdds_solve(c, &G, c->e_b, c->e_u, rtol, maxit, nullptr, stream);
+  if (se != PDDS_OK && se != PDDS_ENOCONV) return se;
+  (void)launches;
+  if (rp_host) CK(c, cudaMemcpyAsync(rp_host, c->e_rp, (n + 1) * 4, cudaMemcpyDeviceToHost, s));
+  if (col_host) CK(c, cudaMemcpyAsync(col_host, c->e_col, nnz * 4, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(val_host, c->e_val, nnz * 8, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(b_host, c->e_b, n * 8, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemcpyAsync(u_host, c->e_u, n * 8, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  return se;
+}
+
+pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
+                                const int64_t* const* N, int64_t Nu, double dt, uint64_t seed,
+                                pdds_csr* const* G, double* const* b, void* stream) {
+  if (!ctxs || count < 1 || !ctxs[0] || !G || !b)
+    return fail(nullptr, PDDS_EINVAL, "assemble_batch: need count >= 1 contexts, G and b");
+  pdds_ctx* c0 = ctxs[0];
+  (void)cudaGetLastError();
+  if (!(dt > 0)) return fail(c0, PDDS_EINVAL, "assemble_batch: dt must be > 0");
+  int max_slots = 0, tw = 0, th = 0;
+  int64_t kmax = 0;
+  for (int i = 0; i < count; ++i) {
+    pdds_ctx* c = ctxs[i];
+    if (!c) return fail(c0, PDDS_EINVAL, "assemble_batch: NULL context in the list");
+    if (c->coef_id != c0->coef_id)
+      return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same coefficient set");
+    if (c->device != c0->device)
+      return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same device");
+    if (pdds_status e = check_csr(c, G[i], b[i])) return fail(c0, e, c->err);
+    if (!(N && N[i]) && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
+      return fail(c0, PDDS_EINVAL, "assemble_batch: n_paths must be in [1, 2^31)");
+    max_slots = std::max(max_slots, c->geo.max_slots);
+    tw = std::max(tw, c->tile_w);
+    th = std::max(th, c->tile_h);
+    kmax = std::max(kmax, c->k_max > 0 ? c->k_max : default_kmax(c, dt));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // Graph key: everything the captured sequence depends on.
+  std::vector<uint64_t> key = {(uint64_t)count, (uint64_t)Nu, (uint64_t)seed, (uint64_t)kmax,
+                               (uint64_t)c0->block, (uint64_t)c0->ctas_per_sm,
+                               (uint64_t)c0->unit_paths, (uint64_t)c0->exit_batch};
+  uint64_t dtb;
+  std::memcpy(&dtb, &dt, 8);
+  key.push_back(dtb);
+  for (int i = 0; i < count; ++i) {
+    key.push_back((uint64_t)(uintptr_t)ctxs[i]);
+    key.push_back((uint64_t)(uintptr_t)(N ? N[i] : nullptr));
+    key.push_back((uint64_t)(uintptr_t)G[i]->val);
+    key.push_back((uint64_t)(uintptr_t)G[i]->row_ptr);
+    key.push_back((uint64_t)(uintptr_t)G[i]->col);
+    key.push_back((uint64_t)(uintptr_t)b[i]);
+  }
+  if (!(c0->graph && key == c0->graph_key)) {
+    if (c0->graph) { cudaGraphExecDestroy(c0->graph); c0->graph = nullptr; }
+    std::vector<ProbDesc> probs(count);
+    for (int i = 0; i < count; ++i) {
+      pdds_ctx* c = ctxs[i];
+      ProbDesc D = make_prob(c, i);
+      D.Gval = G[i]->val;
+      D.b = b[i];
+      D.n_per_knot = N ? N[i] : nullptr;
+      D.n_paths = Nu;
+      if (D.n_per_knot) {
+        D.knot_unit_prefix = c->d_unit_prefix;
+        D.path_prefix = c->d_path_prefix;
+      } else {
+        D.units_per_knot = ceil_div(Nu, c0->unit_paths);
+      }
+      probs[i] = D;
+    }
+    if (c0->batch_cap < count) {
+      cudaFree(c0->d_batch);
+      c0->d_batch = nullptr;
+      CK(c0, dalloc(&c0->d_batch, count));
+      cudaFree(c0->d_prob_prefix);
+      c0->d_prob_prefix = nullptr;
+      CK(c0, dalloc(&c0->d_prob_prefix, count + 1));
+      c0->batch_cap = count;
+    }
+    CK(c0, cudaStreamSynchronize(s));  // a previous replay may still read the old table
+    CK(c0, cudaMemcpy(c0->d_batch, probs.data(), count * sizeof(ProbDesc), cudaMemcpyHostToDevice));
+    const size_t sb = [&] {
+      size_t x = pdds::stage_header_bytes() + round_up((size_t)max_slots * 8, 128);
+      if (c0->coef_id == PDDS_COEF_TABLE) x += 2 * round_up((size_t)tw * th * 4, 128);
+      return round_up(x, 128);
+    }();
+    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, 2 * sb));
+    // Capture on a private non-blocking stream (the legacy default stream
+    // cannot be captured); the instantiated graph is launched on the caller's.
+    if (!c0->cap_stream) CK(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t user_stream = s;
+    (void)user_stream;
+    cudaStream_t s = c0->cap_stream;
+    cudaGraph_t graph;
+    CK(c0, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    pdds_status cap = PDDS_OK;
+    auto step = [&](cudaError_t e, const char* what) {
+      if (e != cudaSuccess && cap == PDDS_OK) cap = cuda_fail(c0, e, what);
+    };
+    for (int i = 0; i < count; ++i) {
+      pdds_ctx* c = ctxs[i];
+      step(cudaMemcpyAsync(G[i]->row_ptr, c->d_row_ptr, (c->geo.n + 1) * 4,
+                           cudaMemcpyDeviceToDevice, s), "pattern copy");
+      step(cudaMemcpyAsync(G[i]->col, c->d_col, c->geo.nnz * 4, cudaMemcpyDeviceToDevice, s),
+           "pattern copy");
+      step(cudaMemsetAsync(G[i]->val, 0, c->geo.nnz * 8, s), "memset");
+      step(cudaMemsetAsync(b[i], 0, c->geo.n * 8, s), "memset");
+      if (N && N[i])
+        step(pdds::launch_unit_prefix(N[i], c->geo.n, c0->unit_paths, c->d_unit_prefix,
+                                      c->d_path_prefix, s), "unit prefix");
+    }
+    step(cudaMemsetAsync(c0->d_scratch, 0, sizeof(pdds::Scratch), s), "memset");
+    step(pdds::launch_prob_prefix(c0->d_batch, count, c0->d_prob_prefix, s), "prob prefix");
+    if (cap == PDDS_OK) {
+      const bool timing = c0->timing;
+      c0->timing = false;
+      cap = run_paths(c0, probs[0], c0->d_batch, count, dt, seed, kmax, nullptr, s, sb, max_slots,
+                      tw, th, c0->coef_id);
+      c0->timing = timing;
+    }
+    for (int i = 0; i < count && cap == PDDS_OK; ++i) {
+      pdds_ctx* c = ctxs[i];
+      step(pdds::launch_finalize(G[i]->row_ptr, G[i]->col, G[i]->val, b[i], N ? N[i] : nullptr,
+                                 Nu, c->geo.n, s), "finalize");
+    }
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (cap != PDDS_OK) { if (ee == cudaSuccess) cudaGraphDestroy(graph); return cap; }
+    CK(c0, ee);
+    cudaError_t ie = cudaGraphInstantiate(&c0->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(c0, ie);
+    c0->graph_key = key;
+  }
+  c0->st = pdds_stats_t{};
+  if (c0->timing) CK(c0, cudaEventRecord(c0->ev0, s));
+  CK(c0, cudaGraphLaunch(c0->graph, s));
+  if (c0->timing) {
+    CK(c0, cudaEventRecord(c0->ev1, s));
+    CK(c0, cudaEventSynchronize(c0->ev1));
+    CK(c0, cudaEventElapsedTime(&c0->st.path_kernel_ms, c0->ev0, c0->ev1));
+  }
+  int launches = 2 + count;
+  for (int i = 0; i < count; ++i) launches += (N && N[i]) ? 1 : 0;
+  c0->st.kernel_launches = launches;
+  return PDDS_OK;
+}
+
+}  // extern "C"

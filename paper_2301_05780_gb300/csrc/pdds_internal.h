@@ -1,0 +1,122 @@
+// Internal data layout shared by the host setup and the CUDA kernels of the
+// PDDSparse assembly library (not part of the public C ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdds {
+
+constexpr int kSides = 4;  // patch sides in the order E, N, W, S (Eq. 14)
+
+// One interfacial knot and its patch, as the path kernel needs them (128 B).
+// The patch box is stored relative to the knot in FP32 so that paths can be
+// integrated in knot-relative coordinates, which keeps FP32 rounding of the
+// position ~1e-9 instead of ~6e-8 in absolute coordinates.
+struct alignas(16) KnotDesc {
+  float xk, yk;            // absolute knot position (FP32, for coefficients)
+  float box[4];            // x_lo, x_hi, y_lo, y_hi of the patch, relative to the knot
+  int32_t ki, kj;          // lattice coordinates of the knot
+  int32_t line[kSides];    // fixed lattice coordinate of each side's grid line
+  int32_t a[kSides];       // stencil lattice range [a, b] along the side's line (Eq. 17)
+  int32_t b[kSides];
+  int32_t off[kSides];     // first accumulator slot of each interface side
+  int32_t slot_base;       // offset of this knot's slots in the slot->CSR map
+  int32_t nslots;          // slots of this knot (sum over interface sides of b-a+1)
+  int32_t dirbits;         // bit o: side o lies on the boundary of Omega (Dirichlet)
+  int32_t tile_i0, tile_j0;  // TABLE: table node of the tile's lower-left corner
+  float tab_fx, tab_fy;    // TABLE: knot position in tile-local node units
+  int32_t pad_;
+};
+static_assert(sizeof(KnotDesc) == 128, "KnotDesc layout: 32 words, one per lane");
+
+// One problem (a context) as seen by the kernels.
+struct ProbDesc {
+  int32_t coef_id;
+  int32_t n;               // knots
+  int32_t LX, LY;          // lattice extents Hx*m, Hy*m
+  float params[8];
+  float x0, y0, x1, y1;    // Omega
+  float dx, dy;            // lattice spacing
+  float inv_dx, inv_dy;
+  float tab_inv_dx, tab_inv_dy;   // TABLE: table nodes per unit length
+  int32_t tag;             // Philox counter word 3
+  int32_t pad0_;
+  const KnotDesc* knots;
+  const int32_t* slot2csr; // CSR value index per slot, -1 for boundary points
+  const int64_t* n_per_knot;      // nullable
+  int64_t n_paths;                // uniform budget when n_per_knot == nullptr
+  const int64_t* knot_unit_prefix; // [n+1] units before knot k (per-knot budgets)
+  int64_t units_per_knot;         // uniform budgets
+  const int64_t* path_prefix;     // [n+1] records before knot k (records mode)
+  double* Gval;
+  double* b;
+  const CUtensorMap* tmap;        // TABLE: [2] = sigma, c (device global memory)
+  int32_t tab_nx, tab_ny;        // TABLE: table nodes
+  const int32_t* col;             // CSR column of each value (records mode)
+};
+
+// Device-side counters of one launch (zeroed before each assemble).
+struct Scratch {
+  unsigned long long next_unit;   // global work queue
+  unsigned long long steps;
+  unsigned long long paths;
+  unsigned long long truncated;
+  unsigned long long clamped;
+  unsigned long long units;
+  int32_t error;                  // 0 or PDDS_ETIMEOUT
+  int32_t pad_;
+};
+
+struct PathRecordDev {
+  int32_t steps, side_flags, col_a, col_b;
+  float w_a, w_b, b_contrib, Y;
+};
+
+struct KParams {
+  ProbDesc prob0;                   // the problem when nprob == 1
+  const ProbDesc* probs;            // device array when nprob > 1
+  const int64_t* prob_unit_prefix;  // [nprob+1]
+  int32_t nprob;
+  int32_t exit_batch;
+  int64_t total_units;
+  int64_t unit_paths;
+  Scratch* scratch;
+  PathRecordDev* records;
+  uint32_t key0, key1;
+  float h, sqh;
+  int64_t kmax;
+  int32_t max_slots;       // accumulator slots per stage
+  int32_t tile_w, tile_h;  // TABLE tile (nodes)
+  int32_t stage_bytes;     // bytes per stage in dynamic shared memory
+  int32_t rec_mode;
+  int32_t pad_;
+  uint64_t wait_ns;        // bound on any device-side wait
+};
+
+// Launchers implemented in the .cu files (host-callable).
+cudaError_t launch_path_kernel(int coef_id, bool records, const KParams& kp, int grid, int block,
+                               size_t smem, cudaStream_t stream);
+cudaError_t path_kernel_occupancy(int coef_id, bool records, int block, size_t smem,
+                                  int* ctas_per_sm);
+cudaError_t set_path_kernel_smem(int coef_id, bool records, size_t smem);
+cudaError_t launch_unit_prefix(const int64_t* n_per_knot, int64_t n, int64_t unit_paths,
+                               int64_t* knot_unit_prefix, int64_t* path_prefix,
+                               cudaStream_t stream);
+cudaError_t launch_prob_prefix_single(const ProbDesc& D, int64_t* out, cudaStream_t stream);
+cudaError_t launch_prob_prefix(const ProbDesc* probs, int nprob, int64_t* out, cudaStream_t stream);
+size_t stage_header_bytes();
+cudaError_t launch_finalize(const int32_t* row_ptr, const int32_t* col, double* val, double* b,
+                            const int64_t* n_per_knot, int64_t n_paths, int64_t n,
+                            cudaStream_t stream);
+
+// FP64 BiCGSTAB building blocks (pdds_solve.cu).
+struct SolveScalars;
+cudaError_t bicgstab_device(const int32_t* row_ptr, const int32_t* col, const double* val,
+                            const double* b, double* x, int64_t n, double* work,
+                            SolveScalars* sc, double rtol, int32_t maxit, int32_t* iters,
+                            double* relres, int* converged, int* launches, cudaStream_t stream);
+size_t bicgstab_work_doubles(int64_t n);
+size_t bicgstab_scalars_bytes();
+
+}  // namespace pdds

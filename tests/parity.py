@@ -1,0 +1,72 @@
+"""Shared helpers of the GPU-vs-oracle parity tests.
+
+Protocol (G and b are random, so the oracle is the same estimator on the same
+Philox streams, in FP64): every path is simulated by both sides; paths whose
+step count or exit side differ (an FP32 position landing on the other side of
+a patch boundary than the FP64 one) are flagged; each side then removes the
+flagged paths' contributions from its OWN sums, using its own per-path
+records, and the remaining sums are compared entry by entry.  The oracle never
+receives anything computed by the GPU.
+
+Tolerance (derived from FP32 path arithmetic, accumulated in FP64): a path's
+weights and b-contribution carry a relative error of ~1e-6, so each raw sum
+over paths must agree to 1e-4 relative, with an absolute floor of 1e-5 in
+per-path units (entries fed by a handful of near-zero weights); b uses the
+same relative bound on the sum of |contributions| to allow for cancellation.
+"""
+import numpy as np
+
+RTOL = 1e-4
+ATOL_RAW = 1e-5
+
+
+def dense_rows(row_ptr, col, val, rows, n):
+    out = np.zeros((len(rows), n))
+    for r, k in enumerate(rows):
+        s, e = row_ptr[k], row_ptr[k + 1]
+        out[r, col[s:e]] = val[s:e]
+    return out
+
+
+def subtract_paths(raw_G, raw_b, rec, sel, rows_index, w_a="w_a", w_b="w_b"):
+    """Remove the contributions of records rec[sel] (row position rows_index)."""
+    for i in np.nonzero(sel)[0]:
+        r = rows_index[i]
+        if rec["col_a"][i] >= 0:
+            raw_G[r, rec["col_a"][i]] -= rec[w_a][i]
+        if rec["col_b"][i] >= 0:
+            raw_G[r, rec["col_b"][i]] -= rec[w_b][i]
+        raw_b[r] -= rec["b_contrib"][i]
+
+
+def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3):
+    """gpu/orc: dicts with row_ptr, col, val (finalized G), b, rec (records for
+    `rows` in order, Nk[r] paths each).  Returns the flagged fraction."""
+    Nk = np.asarray(Nk, dtype=np.int64)
+    rows_index = np.repeat(np.arange(len(rows)), Nk)
+    rg, ro = gpu["rec"], orc["rec"]
+    assert len(rg) == len(ro) == Nk.sum()
+    side_g = rg["side_flags"] & 0xFF
+    flag = (rg["steps"] != ro["steps"]) | (side_g != ro["side"])
+    frac = flag.mean()
+    assert frac <= max_flag_frac, f"flagged fraction {frac:.2e}"
+    # raw sums: -G_kj N_k and b_k N_k
+    Gg = -dense_rows(gpu["row_ptr"], gpu["col"], gpu["val"], rows, n) * Nk[:, None]
+    Go = -dense_rows(orc["row_ptr"], orc["col"], orc["val"], rows, n) * Nk[:, None]
+    for r, k in enumerate(rows):
+        Gg[r, k] = 0.0
+        Go[r, k] = 0.0
+    bg = np.asarray(gpu["b"])[rows] * Nk
+    bo = np.asarray(orc["b"])[rows] * Nk
+    subtract_paths(Gg, bg, rg, flag, rows_index)
+    subtract_paths(Go, bo, ro, flag, rows_index)
+    err = np.abs(Gg - Go)
+    bad = err > RTOL * np.abs(Go) + ATOL_RAW
+    assert not bad.any(), (f"G mismatch at {np.argwhere(bad)[:5].tolist()}: gpu "
+                           f"{Gg[bad][:5]} oracle {Go[bad][:5]}")
+    babs = np.bincount(rows_index[~flag], weights=np.abs(ro["b_contrib"][~flag]),
+                       minlength=len(rows))
+    berr = np.abs(bg - bo)
+    bbad = berr > RTOL * babs + ATOL_RAW
+    assert not bbad.any(), f"b mismatch rows {np.nonzero(bbad)[0][:5]}: {bg[bbad]} vs {bo[bbad]}"
+    return frac
