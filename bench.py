@@ -223,6 +223,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args.config)
     w.seed = replica_seed(w.seed, rank)       # independent replica per rank
+    if args.paths:
+        w.n_paths = args.paths
     P = pdds.Problem(w, device=local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
@@ -271,16 +273,17 @@ def run_gpu(args):
     bh = torch.empty(n, dtype=torch.float64, **pin)
     uh = torch.empty(n, dtype=torch.float64, **pin)
     pdds.pdds_set_timing(P.ctx, False)
-    e2e_steps = max(2, min(args.steps, 5))
-    pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 5000, rp, col, val, bh, uh,
-                                  n_per_knot=Nh)
-    torch.cuda.synchronize()
+    e2e_steps = 0 if args.no_baseline else max(2, min(args.steps, 5))
+    if e2e_steps:
+        pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 5000, rp, col, val, bh, uh,
+                                      n_per_knot=Nh)
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 5000, rp, col, val, bh, uh,
                                       n_per_knot=Nh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_val = steps_done / args.steps / e2e_s * world
+    e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
+    e2e_val = steps_done / args.steps / e2e_s * world if e2e_steps else None
     h2d = n * 8
     d2h = (n + 1) * 4 + nnz * 4 + nnz * 8 + 2 * n * 8
 
@@ -302,7 +305,7 @@ def run_gpu(args):
     achieved = flops_launch / kernel_s / 1e12
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    cpu = cpu_baseline(w) if world == 1 or rank == 0 else None
+    cpu = None if args.no_baseline else cpu_baseline(w)
     line = {
         "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -337,6 +340,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg4", "cfg5"])
+    ap.add_argument("--paths", type=int, default=0,
+                    help="override paths per knot (small profiling cases; not a bench line)")
+    ap.add_argument("--no-baseline", action="store_true",
+                    help="skip the CPU-oracle baseline and the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

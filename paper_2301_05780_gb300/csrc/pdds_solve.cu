@@ -88,12 +88,12 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ r,
     p[i] = r[i] + beta * (p[i] - om * v[i]);
 }
 
-// y = A x (one warp per row) and (w1, y), (w2, y) accumulated.
+// y = A x (one warp per row), with (w1, y) and, if `self_dot`, (y, y)
+// accumulated.  y never aliases x or w1; (y, y) is taken from the register.
 __global__ void k_spmv_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const double* __restrict__ x,
-                           double* __restrict__ y, const double* __restrict__ w1,
-                           const double* __restrict__ w2, int64_t n, double* acc1, double* acc2,
-                           const SolveScalars* sc) {
+                           double* __restrict__ y, const double* __restrict__ w1, int self_dot,
+                           int64_t n, double* acc1, double* acc2, const SolveScalars* sc) {
   if (sc->converged | sc->breakdown) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -105,7 +105,7 @@ __global__ void k_spmv_dot(const int32_t* __restrict__ rp, const int32_t* __rest
     if (lane == 0) {
       y[row] = s;
       a1 += w1[row] * s;
-      if (w2) a2 += w2[row] * s;
+      if (self_dot) a2 += s * s;
     }
   }
   block_add3(a1, a2, 0.0, acc1, acc2, nullptr);
@@ -197,10 +197,10 @@ cudaError_t bicgstab_device(const int32_t* rp, const int32_t* ci, const double* 
     const int m = std::min(chunk, maxit - it);
     for (int j = 0; j < m; ++j) {
       k_update_p<<<vgrid, kThreads, 0, st>>>(p, r, v, n, sc);
-      k_spmv_dot<<<mgrid, kThreads, 0, st>>>(rp, ci, val, p, v, rh, nullptr, n, &sc->d_rv,
+      k_spmv_dot<<<mgrid, kThreads, 0, st>>>(rp, ci, val, p, v, rh, 0, n, &sc->d_rv,
                                               nullptr, sc);
       k_s<<<vgrid, kThreads, 0, st>>>(s, r, v, n, sc);
-      k_spmv_dot<<<mgrid, kThreads, 0, st>>>(rp, ci, val, s, t, s, t, n, &sc->d_ts, &sc->d_tt, sc);
+      k_spmv_dot<<<mgrid, kThreads, 0, st>>>(rp, ci, val, s, t, s, 1, n, &sc->d_ts, &sc->d_tt, sc);
       k_xr<<<vgrid, kThreads, 0, st>>>(x, r, rh, p, s, t, n, sc);
       k_scalars<<<1, 1, 0, st>>>(sc);
       nl += 6;
