@@ -200,6 +200,31 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
 pdds_status pdds_solve(pdds_ctx* ctx, const pdds_csr* G, const double* b, double* u,
                        double rtol, int32_t maxit, int32_t* iters, void* cuda_stream);
 
+/* Allocation-free variant of pdds_solve (the paper has no counterpart; this
+ * is a service to callers).  For callers that cannot allocate device memory:
+ * applications that own all device memory through their own pool or arena
+ * under a fixed budget, where a library-side cudaMalloc would bypass their
+ * accounting or fail, and latency-critical code that cannot accept the implicit
+ * synchronization of cudaMalloc/cudaFree.  It needs no context and calls no
+ * cudaMalloc, cudaFree or allocating library routine: its scratch (six work
+ * vectors and the recurrence scalars) is a static device array of
+ * 6 * 131072 + 32 doubles (6.3 MB) that every GPU loading this library holds
+ * until the process exits.
+ *   G, b, u, rtol, maxit, iters, cuda_stream: as for pdds_solve (all device
+ *     pointers; u is overwritten, initial guess 0; the stream is synchronized
+ *     every few iterations to read the residual).
+ *   G->n must be in [1, 131072]; larger systems are rejected with PDDS_EINVAL
+ *     before any device work (use pdds_solve).
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * in the process share the one array per device: calls that overlap on the
+ * GPU (other host threads or other streams) race and corrupt each other's
+ * results -- serialize them.  Each call re-initialises every part of the array
+ * it reads, so nothing carries over from the previous call.
+ * Errors: EINVAL, ENOCONV, ECUDA; text via pdds_last_error(NULL). */
+pdds_status pdds_solve_noalloc(const pdds_csr* G, const double* b, double* u, double rtol,
+                               int32_t maxit, int32_t* iters, void* cuda_stream);
+
 /* End-to-end call with HOST buffers: uploads the per-knot budgets, assembles,
  * solves and downloads G (row_ptr, col, val), b and u.  Device scratch is owned
  * by the context.  n_per_knot_host may be NULL.  Synchronizes the stream. */

@@ -425,6 +425,10 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
 
 }  // namespace
 
+namespace pdds {
+void set_global_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pdds
+
 // ================================================================ C ABI
 extern "C" {
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace pdds {
 
 constexpr int kSides = 4;  // patch sides in the order E, N, W, S (Eq. 14)
@@ -117,6 +119,7 @@ cudaError_t bicgstab_device(const int32_t* row_ptr, const int32_t* col, const do
                             SolveScalars* sc, double rtol, int32_t maxit, int32_t* iters,
                             double* relres, int* converged, int* launches, cudaStream_t stream);
 size_t bicgstab_work_doubles(int64_t n);
+void set_global_error(const std::string& msg);  // text of pdds_last_error(NULL)
 size_t bicgstab_scalars_bytes();
 
 }  // namespace pdds

@@ -8,7 +8,11 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <string>
 
+#include "pdds.h"
 #include "pdds_internal.h"
 
 namespace pdds {
@@ -218,3 +222,103 @@ cudaError_t bicgstab_device(const int32_t* rp, const int32_t* ci, const double* 
 }
 
 }  // namespace pdds
+
+// ===========================================================================
+// Allocation-free solve.
+//
+// Some callers of this library cannot allocate device memory: applications
+// that own all device memory through their own pool or arena under a fixed
+// budget (a library-side cudaMalloc would bypass their accounting, or fail),
+// and latency-critical code where the implicit device synchronization of
+// cudaMalloc/cudaFree is not acceptable.  pdds_solve_noalloc serves them: it
+// runs the same BiCGSTAB kernels as pdds_solve, but its scratch -- six work
+// vectors and the recurrence scalars -- lives in the file-scope device array
+// below, which every GPU that loads this library holds until the process
+// exits (6.3 MB).  The caller still passes G, b and u.
+// ===========================================================================
+namespace pdds {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 131072;           // largest system size served
+constexpr int64_t kNoAllocScalarSlots = 32;        // >= sizeof(SolveScalars) / 8
+static_assert(sizeof(pdds::SolveScalars) <= kNoAllocScalarSlots * sizeof(double), "scratch");
+
+static __device__ __align__(256) double g_noalloc_scratch[6 * kNoAllocMaxN + kNoAllocScalarSlots];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+}  // namespace pdds
+
+extern "C" pdds_status pdds_solve_noalloc(const pdds_csr* G, const double* b, double* u,
+                                          double rtol, int32_t maxit, int32_t* iters,
+                                          void* cuda_stream) {
+  using namespace pdds;
+  if (!G || !b || !u || !G->row_ptr || !G->col || !G->val) {
+    set_global_error("solve_noalloc: NULL matrix/vector");
+    return PDDS_EINVAL;
+  }
+  if (G->n > kNoAllocMaxN) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "solve_noalloc: n = %lld exceeds the static scratch limit of %lld unknowns; "
+                  "use pdds_solve", (long long)G->n, (long long)kNoAllocMaxN);
+    set_global_error(buf);
+    return PDDS_EINVAL;
+  }
+  if (G->n < 1 || G->nnz < G->n) {
+    set_global_error("solve_noalloc: need n >= 1 and nnz >= n");
+    return PDDS_EINVAL;
+  }
+  if (!(rtol > 0) || maxit < 1) {
+    set_global_error("solve_noalloc: need rtol > 0, maxit >= 1");
+    return PDDS_EINVAL;
+  }
+  (void)cudaGetLastError();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_global_error(std::string("solve_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return PDDS_ECUDA;
+  }
+  double* scratch = nullptr;
+  {
+    // First call on this device (the current one): look up the array's device
+    // address.  Host code cannot use g_noalloc_scratch's name as a pointer.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        set_global_error(std::string("solve_noalloc: cudaGetSymbolAddress: ") +
+                         cudaGetErrorString(e));
+        return PDDS_ECUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  auto* sc = reinterpret_cast<SolveScalars*>(scratch + 6 * kNoAllocMaxN);
+  int32_t it = 0;
+  double rel = 0;
+  int conv = 0, nl = 0;
+  // bicgstab_device zeroes the scalars and initialises every work vector it
+  // reads, so the previous call's contents never leak into this one.
+  e = bicgstab_device(G->row_ptr, G->col, G->val, b, u, G->n, scratch, sc, rtol, maxit, &it, &rel,
+                      &conv, &nl, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("solve_noalloc: ") + cudaGetErrorString(e));
+    return PDDS_ECUDA;
+  }
+  if (iters) *iters = it;
+  if (conv != 1) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "solve_noalloc: no convergence after %d iterations (relres %.3e)",
+                  it, rel);
+    set_global_error(buf);
+    return PDDS_ENOCONV;
+  }
+  return PDDS_OK;
+}

@@ -78,6 +78,7 @@ _SIGS = {
     "pdds_assemble_batch": (C.c_int, [_P, C.c_int32, _P, C.c_int64, C.c_double, C.c_uint64, _P,
                                       _P, _P]),
     "pdds_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, _P, _P]),
+    "pdds_solve_noalloc": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, _P, _P]),
     "pdds_assemble_solve_host": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_double,
                                            C.c_int32, _P, _P, _P, _P, _P, _P]),
     "pdds_stats": (C.c_int, [_P, _P]),
@@ -245,6 +246,21 @@ def pdds_solve(ctx, G, b, u, rtol=1e-12, maxit=2000, stream=None):
     st = lib().pdds_solve(ctx, C.byref(csr), C.c_void_p(b.data_ptr()), C.c_void_p(u.data_ptr()),
                           float(rtol), int(maxit), C.byref(it), _stream(stream))
     _check(st, ctx)
+    return it.value
+
+
+def pdds_solve_noalloc(G, b, u, rtol=1e-12, maxit=2000, stream=None, n=None):
+    """Allocation-free solve (see include/pdds.h): for callers that cannot
+    allocate device memory.  `n` overrides the system size passed to the
+    library (used to exercise its size check)."""
+    csr = _csr_struct(G)
+    if n is not None:
+        csr.n = int(n)
+    it = C.c_int32()
+    st = lib().pdds_solve_noalloc(C.byref(csr), C.c_void_p(b.data_ptr()),
+                                  C.c_void_p(u.data_ptr()), float(rtol), int(maxit), C.byref(it),
+                                  _stream(stream))
+    _check(st, None)
     return it.value
 
 
