@@ -349,7 +349,30 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "cfg5":
+        return run_cv_study(args)
     return run_gpu(args)
+
+
+def run_cv_study(args):
+    """Config 5: plain estimator vs the learned control variate, time to the
+    same interfacial statistical error (one JSON line; not the default bench)."""
+    import torch
+    from paper_2301_05780_gb300 import cv
+    torch.cuda.set_device(0)
+    w = workload("cfg5")
+    n_plain = args.paths or w.n_paths
+    res = cv.study(w, n_plain)
+    plain = res["plain"]
+    line = {"metric": METRIC, "value": plain["path_steps"] / (plain["kernel_ms"] * 1e-3),
+            "unit": "path-steps/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": plain["assembly_solve_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "knots": res["knots"], "dt": w.dt,
+                       "paths_per_knot": n_plain},
+            "cv_study": res}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

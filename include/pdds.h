@@ -200,6 +200,43 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
 pdds_status pdds_solve(pdds_ctx* ctx, const pdds_csr* G, const double* b, double* u,
                        double rtol, int32_t maxit, int32_t* iters, void* cuda_stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned control variate (Eq. 11, 37-39).  The paper adds to each score the */
+/* Ito integral xi = -int Y F . dW with F = sigma^T grad u0, u0 a warm-up     */
+/* solution (Sec. 4.2); here u0 is a small network v_theta : R^2 -> R,        */
+/* 2 -> 64 -> 64 -> 1 with SiLU, fitted to warm-up nodal values and boundary  */
+/* samples.  theta is FP32, PDDS_MLP_NPARAM values: W1[64][2], b1[64],         */
+/* W2[64][64] (row = output unit), b2[64], w3[64], b3.                        */
+#define PDDS_MLP_NPARAM 4417
+
+/* Mean-squared-error loss (1/N) sum_p (v(x_p) - target_p)^2 and its gradient
+ * w.r.t. theta (FP32 forward/backward kernels).  All pointers DEVICE:
+ * theta[NPARAM], xy[npts][2], target[npts], grad[NPARAM] (overwritten),
+ * loss (one double, overwritten).  Asynchronous. */
+pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, const float* target,
+                               int64_t npts, float* grad, double* loss, void* cuda_stream);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr)
+ * on the loss above; theta (DEVICE) is updated in place; loss_history_host
+ * (nullable) receives the loss before each step.  Allocates and frees its own
+ * scratch (gradient and Adam moments); synchronizes the stream. */
+pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target, int64_t npts,
+                           int32_t steps, double lr, double* loss_history_host,
+                           void* cuda_stream);
+
+/* v_theta and grad v_theta at npts DEVICE points with the in-path evaluation
+ * (64x64 layer on the tensor cores with BF16 operands and FP32 accumulation;
+ * the rest FP32).  v (nullable) [npts], grad_xy [npts][2].  Synchronizes. */
+pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, float* v,
+                          float* grad_xy, void* cuda_stream);
+
+/* Attach v_theta (DEVICE theta, copied and staged) to the context: from then
+ * on pdds_assemble adds xi_K = -sum_n Y_n s(X_n) grad v(X_n) . dW_n to every
+ * path's b contribution (Eq. 37, left-point Ito sum), which leaves E[b]
+ * unchanged and lowers its variance as v approaches u.  NULL detaches it.
+ * Available for PDDS_COEF_LAPLACE_EXPSIN, _MANUFACTURED and _CONSTANT. */
+pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
+
 /* Allocation-free variant of pdds_solve (the paper has no counterpart; this
  * is a service to callers).  For callers that cannot allocate device memory:
  * applications that own all device memory through their own pool or arena

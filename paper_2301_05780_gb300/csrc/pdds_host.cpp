@@ -237,6 +237,9 @@ struct pdds_ctx {
   int batch_cap = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // control variate (staged network image) and whether it is on
+  void* d_mlp = nullptr;
+  bool cv_on = false;
   std::vector<uint64_t> graph_key;
   pdds_stats_t st{};
   std::string err = "no error";
@@ -271,6 +274,7 @@ void free_ctx(pdds_ctx* c) {
   cudaFree(c->e_val); cudaFree(c->e_b); cudaFree(c->e_u); cudaFree(c->d_batch);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->d_mlp);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -363,16 +367,22 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   kp.rec_mode = rec != nullptr;
   // a wait may outlast the slowest path of a unit: K_max steps at ~4 us
   kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * (double)kmax);
-  const size_t smem = 2 * sbytes;
-  CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, smem));
+  const bool cv = nprob == 1 && c->cv_on;
+  kp.mlp = cv ? c->d_mlp : nullptr;
+  // the control-variate step is ~10x heavier: wait bounds scale with it
+  if (cv && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * (double)kmax);
+  // CV kernels keep the staged network at the start of dynamic shared memory
+  const size_t smem = 2 * sbytes + (cv ? round_up(pdds::mlp_image_bytes(), 128) : 0);
+  CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, smem));
+  const int block = cv ? std::min(c->block, 256) : c->block;  // CV kernels: <= 256 threads
   int per_sm = c->ctas_per_sm;
   if (per_sm <= 0) {
-    CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, c->block, smem, &per_sm));
+    CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, block, smem, &per_sm));
     if (per_sm <= 0) return fail(c, PDDS_EINVAL, "launch: block/shared memory too large");
   }
   const int grid = c->num_sms * per_sm;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
-  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, kp, grid, c->block, smem, stream));
+  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, kp, grid, block, smem, stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
   return PDDS_OK;
 }
@@ -654,6 +664,22 @@ pdds_status pdds_set_wait_limit(pdds_ctx* c, double seconds) {
   return PDDS_OK;
 }
 
+pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_control_variate: NULL context");
+  if (!theta) {
+    c->cv_on = false;
+    return PDDS_OK;
+  }
+  if (!pdds::path_kernel_has_cv(c->coef_id))
+    return fail(c, PDDS_EINVAL, "set_control_variate: not available for this coefficient set");
+  (void)cudaGetLastError();
+  if (!c->d_mlp) CK(c, cudaMalloc(&c->d_mlp, pdds::mlp_image_bytes()));
+  CK(c, pdds::mlp_stage(theta, c->d_mlp, nullptr));
+  CK(c, cudaDeviceSynchronize());
+  c->cv_on = true;
+  return PDDS_OK;
+}
+
 pdds_status pdds_set_timing(pdds_ctx* c, int32_t on) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_timing: NULL context");
   c->timing = on != 0;
@@ -779,6 +805,8 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same coefficient set");
     if (c->device != c0->device)
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same device");
+    if (c->cv_on)
+      return fail(c0, PDDS_EINVAL, "assemble_batch: control variates are not supported in batches");
     if (pdds_status e = check_csr(c, G[i], b[i])) return fail(c0, e, c->err);
     if (!(N && N[i]) && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
       return fail(c0, PDDS_EINVAL, "assemble_batch: n_paths must be in [1, 2^31)");
@@ -837,7 +865,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       if (c0->coef_id == PDDS_COEF_TABLE) x += 2 * round_up((size_t)tw * th * 4, 128);
       return round_up(x, 128);
     }();
-    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, 2 * sb));
+    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, false, 2 * sb));
     // Capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the instantiated graph is launched on the caller's.
     if (!c0->cap_stream) CK(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));

@@ -94,14 +94,19 @@ struct KParams {
   int32_t rec_mode;
   int32_t pad_;
   uint64_t wait_ns;        // bound on any device-side wait
+  const void* mlp;         // staged control-variate network (MlpSmem), or nullptr
 };
 
 // Launchers implemented in the .cu files (host-callable).
-cudaError_t launch_path_kernel(int coef_id, bool records, const KParams& kp, int grid, int block,
-                               size_t smem, cudaStream_t stream);
-cudaError_t path_kernel_occupancy(int coef_id, bool records, int block, size_t smem,
+cudaError_t launch_path_kernel(int coef_id, bool records, bool cv, const KParams& kp, int grid,
+                               int block, size_t smem, cudaStream_t stream);
+cudaError_t path_kernel_occupancy(int coef_id, bool records, bool cv, int block, size_t smem,
                                   int* ctas_per_sm);
-cudaError_t set_path_kernel_smem(int coef_id, bool records, size_t smem);
+cudaError_t set_path_kernel_smem(int coef_id, bool records, bool cv, size_t smem);
+bool path_kernel_has_cv(int coef_id);
+// Control-variate network (pdds_mlp.cu): FP32 theta -> staged image.
+size_t mlp_image_bytes();
+cudaError_t mlp_stage(const float* theta, void* image, cudaStream_t stream);
 cudaError_t launch_unit_prefix(const int64_t* n_per_knot, int64_t n, int64_t unit_paths,
                                int64_t* knot_unit_prefix, int64_t* path_prefix,
                                cudaStream_t stream);

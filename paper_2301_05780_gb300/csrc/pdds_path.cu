@@ -28,12 +28,15 @@
 
 #include "pdds.h"
 #include "pdds_internal.h"
+#include "pdds_mlp.cuh"
 
 namespace pdds {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kFixedOne = 1073741824.0f;             // 2^30: one path's full weight
+constexpr double kFixedInv = 1.0 / 1073741824.0;       // 2^-30
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -106,8 +109,11 @@ struct Smem {
   int* live;    // units loaded (or being loaded) and not yet flushed, this CTA
   int* qempty;  // 1 once a load found the global queue empty
   __device__ Stage& st(int s) const { return *reinterpret_cast<Stage*>(base + s * stage_bytes); }
-  __device__ double* acc(int s) const {
-    return reinterpret_cast<double*>(base + s * stage_bytes + kStageHdr);
+  // Slot accumulators: exact 64-bit fixed point in units of 2^-30 of a path's
+  // weight (weights are <= 1, a unit has <= 2^24 paths, so sums stay < 2^54);
+  // integer shared atomics, independent of the order in which paths finish.
+  __device__ unsigned long long* acc(int s) const {
+    return reinterpret_cast<unsigned long long*>(base + s * stage_bytes + kStageHdr);
   }
   __device__ float* tile(int s, int field) const {
     return reinterpret_cast<float*>(base + s * stage_bytes + kStageHdr + acc_bytes +
@@ -339,8 +345,8 @@ __device__ bool load_unit(const Smem& S, int s, int q, const KParams& P, int64_t
   }
   __syncwarp();
   const int nslots = H.kd.nslots;
-  double* acc = S.acc(s);
-  for (int i = lane; i < nslots; i += 32) acc[i] = 0.0;
+  unsigned long long* acc = S.acc(s);
+  for (int i = lane; i < nslots; i += 32) acc[i] = 0ull;
   if (D.tmap != nullptr) {
     // Stage the patch's sigma and c tiles with TMA (one CTA, no multicast):
     // the patch-local coefficient memory of Sec. 3.3.
@@ -387,12 +393,13 @@ __device__ void flush_unit(const Smem& S, int s, const KParams& P) {
   __threadfence_block();
   Stage& H = S.st(s);
   const ProbDesc& D = prob_desc(P, H.prob);
-  const double* acc = S.acc(s);
+  const unsigned long long* acc = S.acc(s);
   const int32_t* map = D.slot2csr + H.kd.slot_base;
   for (int i = lane; i < H.kd.nslots; i += 32) {
-    const double v = acc[i];
+    const unsigned long long q = acc[i];
     const int c = __ldg(map + i);
-    if (v != 0.0 && c >= 0) atomicAdd(D.Gval + c, v);
+    // exact: q < 2^53, times a power of two
+    if (q != 0ull && c >= 0) atomicAdd(D.Gval + c, (double)q * kFixedInv);
   }
   if (lane == 0) atomicAdd(D.b + H.k, H.bsum);
   __syncwarp();
@@ -410,13 +417,25 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 // ------------------------------------------------------------- the kernel
-template <int COEF, bool RECORD>
-__global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KParams P) {
+// Plain variants: up to 1024 threads (64 registers).  Control-variate variants
+// hold the MMA fragments of the in-path network: at most 256 threads and two
+// CTAs per SM, i.e. up to 128 registers.
+template <int COEF, bool RECORD, bool CV>
+__global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
+    path_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  // Control variate: the network is staged once per CTA at the start of the
+  // dynamic shared memory (CV variants only); the unit ring follows it.
+  MlpSmem* mlp_s = reinterpret_cast<MlpSmem*>(smem_raw);
+  if constexpr (CV) {
+    const int4* src = reinterpret_cast<const int4*>(P.mlp);
+    int4* dst = reinterpret_cast<int4*>(mlp_s);
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
+  }
   Smem S;
-  S.base = smem_raw;
+  S.base = smem_raw + (CV ? kMlpSmemBytes : 0);
   S.stage_bytes = P.stage_bytes;
   S.acc_bytes = ((P.max_slots * 8) + 127) / 128 * 128;
   S.tile_bytes = ((P.tile_w * P.tile_h * 4) + 127) / 128 * 128;
@@ -448,7 +467,7 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
   uint32_t p = 0, kk = 0, tagw = 0;
   int n = 0;
   float xk = 0.f, yk = 0.f, bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
-  float X = 0.f, Y = 0.f, Sx = 0.f, Z = 0.f;
+  float X = 0.f, Y = 0.f, Sx = 0.f, Z = 0.f, XI = 0.f;
   unsigned long long my_steps = 0, my_paths = 0, my_trunc = 0, my_clamp = 0;
   int want = 0;  // warp-uniform: unit sequence number the warp takes paths from
   const int64_t kmax = P.kmax;
@@ -493,7 +512,7 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
         tagw = (uint32_t)H.tag;
         xk = H.kd.xk; yk = H.kd.yk;
         bx0 = H.kd.box[0]; bx1 = H.kd.box[1]; by0 = H.kd.box[2]; by1 = H.kd.box[3];
-        n = 0; X = 0.f; Y = 0.f; Sx = 0.f; Z = 0.f;
+        n = 0; X = 0.f; Y = 0.f; Sx = 0.f; Z = 0.f; XI = 0.f;
       }
       if (base + cnt >= pend) ++want;     // unit fully handed out
       idle = __ballot_sync(kFull, !alive);
@@ -517,7 +536,42 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
     // ---- step until enough lanes have exited -----------------------------
     bool exited = false, trunc = false;
     for (;;) {
-      if (alive && !exited) {
+      if constexpr (CV) {
+        // Same step as below, but the warp stays converged for the tensor-core
+        // evaluation of grad v_theta at every lane's position; only lanes that
+        // are stepping use it: dxi = -Y sigma grad v . dW (Eq. 37).
+        const bool go = alive && !exited;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (go) {
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.key0,
+                                        P.key1);
+          box_muller(r.x, r.y, z[0], z[1]);
+          box_muller(r.z, r.w, z[2], z[3]);
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float gx, gy, vv;
+          mlp_grad_warp<false>(*mlp_s, xk + X, yk + Y, gx, gy, vv);
+          if (go && !exited) {
+            const Stage& H = S.st(st);
+            float s, ddx, ddy, c, f;
+            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, s, ddx, ddy, c, f);
+            const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
+            float Yw = 1.0f;
+            if constexpr (has_potential<COEF>()) {
+              Yw = __expf(Sx);
+              Z = fmaf(-f * Yw, h, Z);
+              Sx = fmaf(c, h, Sx);
+            }
+            XI = fmaf(-Yw * s, fmaf(gx, dWx, gy * dWy), XI);
+            X += fmaf(ddx, h, s * dWx);
+            Y += fmaf(ddy, h, s * dWy);
+            ++n;
+            exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+            if (!exited && n >= kmax) { exited = true; trunc = true; }
+          }
+        }
+      } else if (alive && !exited) {
         const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.key0,
                                       P.key1);
         float z[4];
@@ -554,7 +608,7 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
     if (leaving) {
       const Stage& H = S.st(st);
       const KnotDesc& kd = H.kd;
-      double* acc = S.acc(st);
+      unsigned long long* acc = S.acc(st);
       const float ov[4] = {X - bx1, Y - by1, bx0 - X, by0 - Y};
       int side = -1;
 #pragma unroll
@@ -568,6 +622,7 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
       float Yk = 1.0f;
       if constexpr (has_potential<COEF>()) Yk = __expf(Sx);
       bc = (double)Z;
+      if constexpr (CV) bc += (double)XI;
       const bool vertical = (side == 0 || side == 2);
       int flags = trunc ? 1 : 0;
       int col_a = -1, col_b = -1;
@@ -590,26 +645,31 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
         int t = (int)floorf(sl);
         if (t >= b - a) t = b - a - 1;
         const float lam = sl - (float)t;
-        const double w1 = (double)lam, w0 = 1.0 - w1;
+        // Y (1 - lam) and Y lam in 2^-30 units: q0 + q1 = qY exactly, so the
+        // path deposits its whole weight Y on the two knots (G 1 = b holds
+        // exactly when c = f = 0 and g = 1).
+        const unsigned long long qY = __float2ull_rn(Yk * kFixedOne);
+        const unsigned long long q1 = __float2ull_rn((Yk * lam) * kFixedOne);
+        const unsigned long long qw[2] = {qY - q1, q1};
         const int lmax = vertical ? H.LY : H.LX;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int tl = a + t + q;
-          const double w = q ? w1 : w0;
           if (tl == 0 || tl == lmax) {
             const int li = vertical ? kd.line[side] : tl;
             const int lj = vertical ? tl : kd.line[side];
-            bc += (double)Yk * w *
+            bc += (double)qw[q] * kFixedInv *
                   (double)g_value(H, fmaf((float)li, H.dx, H.x0), fmaf((float)lj, H.dy, H.y0));
           } else {
             const int slot = kd.off[side] + t + q;
-            atomicAdd(acc + slot, (double)Yk * w);
+            atomicAdd(acc + slot, qw[q]);
             if constexpr (RECORD) {
               const ProbDesc& D = prob_desc(P, H.prob);
               const int c = D.slot2csr[kd.slot_base + slot];
               const int col = D.col[c];
-              if (q == 0) { col_a = col; wa = (float)((double)Yk * w); }
-              else { col_b = col; wb = (float)((double)Yk * w); }
+              const float wv = (float)((double)qw[q] * kFixedInv);
+              if (q == 0) { col_a = col; wa = wv; }
+              else { col_b = col; wb = wv; }
             }
           }
         }
@@ -626,20 +686,18 @@ __global__ void __launch_bounds__(1024) path_kernel(const __grid_constant__ KPar
         R.w_a = wa; R.w_b = wb; R.b_contrib = (float)bc; R.Y = Yk;
         P.records[idx] = R;
       }
+      atomicAdd(&S.st(st).bsum, bc);  // one FP64 shared atomic per exit
     }
-    // warp-aggregated b sums and completion counts per stage
+    // warp-aggregated completion counts per stage
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const unsigned m = __ballot_sync(kFull, leaving && st == s);
       if (m == 0) continue;
-      const double tot = warp_sum((leaving && st == s) ? bc : 0.0);
       __syncwarp();
       __threadfence_block();
       int fin = 0;
       if (lane == 0) {
         Stage& H = S.st(s);
-        atomicAdd(&H.bsum, tot);
-        __threadfence_block();
         const int old = atomicAdd(&H.done, __popc(m));
         fin = (old + __popc(m) == H.total);
       }
@@ -720,12 +778,22 @@ __global__ void finalize_kernel(const int32_t* __restrict__ row_ptr, const int32
   if (lane == 0) b[k] *= inv;
 }
 
-template <int COEF, bool REC>
+template <int COEF, bool REC, bool CV = false>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&path_kernel<COEF, REC>);
+  return reinterpret_cast<void*>(&path_kernel<COEF, REC, CV>);
 }
 
-void* pick(int coef, bool rec) {
+// Control-variate variants exist for the analytic sets used with a learned
+// v_theta (config 5 uses the manufactured set) and for the test set.
+void* pick(int coef, bool rec, bool cv) {
+  if (cv) {
+    switch (coef) {
+      case PDDS_COEF_LAPLACE_EXPSIN: return rec ? kernel_ptr<0, true, true>() : kernel_ptr<0, false, true>();
+      case PDDS_COEF_MANUFACTURED: return rec ? kernel_ptr<1, true, true>() : kernel_ptr<1, false, true>();
+      case PDDS_COEF_CONSTANT: return rec ? kernel_ptr<4, true, true>() : kernel_ptr<4, false, true>();
+      default: return nullptr;
+    }
+  }
   switch (coef) {
     case PDDS_COEF_LAPLACE_EXPSIN: return rec ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
     case PDDS_COEF_MANUFACTURED: return rec ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
@@ -738,22 +806,24 @@ void* pick(int coef, bool rec) {
 
 }  // namespace
 
-cudaError_t launch_path_kernel(int coef, bool rec, const KParams& kp, int grid, int block,
+bool path_kernel_has_cv(int coef) { return pick(coef, false, true) != nullptr; }
+
+cudaError_t launch_path_kernel(int coef, bool rec, bool cv, const KParams& kp, int grid, int block,
                                size_t smem, cudaStream_t stream) {
-  void* fn = pick(coef, rec);
+  void* fn = pick(coef, rec, cv);
   if (!fn) return cudaErrorInvalidValue;
   void* args[] = {const_cast<KParams*>(&kp)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
-cudaError_t path_kernel_occupancy(int coef, bool rec, int block, size_t smem, int* ctas) {
-  void* fn = pick(coef, rec);
+cudaError_t path_kernel_occupancy(int coef, bool rec, bool cv, int block, size_t smem, int* ctas) {
+  void* fn = pick(coef, rec, cv);
   if (!fn) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
 }
 
-cudaError_t set_path_kernel_smem(int coef, bool rec, size_t smem) {
-  void* fn = pick(coef, rec);
+cudaError_t set_path_kernel_smem(int coef, bool rec, bool cv, size_t smem) {
+  void* fn = pick(coef, rec, cv);
   if (!fn) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }

@@ -79,6 +79,10 @@ _SIGS = {
                                       _P, _P]),
     "pdds_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, _P, _P]),
     "pdds_solve_noalloc": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, _P, _P]),
+    "pdds_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "pdds_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
+    "pdds_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "pdds_set_control_variate": (C.c_int, [_P, _P]),
     "pdds_assemble_solve_host": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_double,
                                            C.c_int32, _P, _P, _P, _P, _P, _P]),
     "pdds_stats": (C.c_int, [_P, _P]),
@@ -262,6 +266,45 @@ def pdds_solve_noalloc(G, b, u, rtol=1e-12, maxit=2000, stream=None, n=None):
                                   _stream(stream))
     _check(st, None)
     return it.value
+
+
+MLP_NPARAM = 4417
+
+
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def pdds_mlp_loss_grad(theta, xy, target, stream=None):
+    """(loss, grad) of the MSE fit of v_theta (device float32 tensors)."""
+    import torch
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=theta.device)
+    loss = torch.empty(1, dtype=torch.float64, device=theta.device)
+    _check(lib().pdds_mlp_loss_grad(_dptr(theta), _dptr(xy), _dptr(target), target.numel(),
+                                    _dptr(grad), _dptr(loss), _stream(stream)))
+    return loss, grad
+
+
+def pdds_mlp_train(theta, xy, target, steps, lr=3e-3, stream=None):
+    """Adam on theta in place; returns the loss history (numpy)."""
+    hist = np.zeros(int(steps))
+    _check(lib().pdds_mlp_train(_dptr(theta), _dptr(xy), _dptr(target), target.numel(),
+                                int(steps), float(lr), hist.ctypes.data, _stream(stream)))
+    return hist
+
+
+def pdds_mlp_eval(theta, xy, stream=None):
+    """(v, grad) at the points xy [n, 2] with the in-path tensor-core routine."""
+    import torch
+    n = xy.shape[0]
+    v = torch.empty(n, dtype=torch.float32, device=xy.device)
+    g = torch.empty(n, 2, dtype=torch.float32, device=xy.device)
+    _check(lib().pdds_mlp_eval(_dptr(theta), _dptr(xy), n, _dptr(v), _dptr(g), _stream(stream)))
+    return v, g
+
+
+def pdds_set_control_variate(ctx, theta):
+    _check(lib().pdds_set_control_variate(ctx, _dptr(theta)), ctx)
 
 
 def pdds_assemble_solve_host(ctx, n_paths, dt, seed, rtol, maxit, row_ptr, col, val, b, u,

@@ -8,16 +8,18 @@ flagged paths' contributions from its OWN sums, using its own per-path
 records, and the remaining sums are compared entry by entry.  The oracle never
 receives anything computed by the GPU.
 
-Tolerance (derived from FP32 path arithmetic, accumulated in FP64): a path's
-weights and b-contribution carry a relative error of ~1e-6, so each raw sum
-over paths must agree to 1e-4 relative, with an absolute floor of 1e-5 in
-per-path units (entries fed by a handful of near-zero weights); b uses the
-same relative bound on the sum of |contributions| to allow for cancellation.
+Tolerance (derived from FP32 path arithmetic, accumulated in FP64): each raw
+sum over paths must agree to 1e-4 relative.  A single path's weights are FP32
+numbers whose rounding, carried along thousands of steps, reaches ~6e-5 of a
+unit weight on the longest paths (measured on the tabulated set), so entries
+whose whole sum is a fraction of one path's weight get an absolute floor of
+1e-4 per-path units, i.e. 1e-4 / N_k in G; b uses the same relative bound on
+the sum of |contributions| to allow for cancellation.
 """
 import numpy as np
 
 RTOL = 1e-4
-ATOL_RAW = 1e-5
+ATOL_RAW = 1e-4
 
 
 def dense_rows(row_ptr, col, val, rows, n):
@@ -39,9 +41,11 @@ def subtract_paths(raw_G, raw_b, rec, sel, rows_index, w_a="w_a", w_b="w_b"):
         raw_b[r] -= rec["b_contrib"][i]
 
 
-def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3):
+def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None):
     """gpu/orc: dicts with row_ptr, col, val (finalized G), b, rec (records for
-    `rows` in order, Nk[r] paths each).  Returns the flagged fraction."""
+    `rows` in order, Nk[r] paths each).  b_extra_tol (per row, raw units) widens
+    the b bound where part of b is computed at lower precision on purpose (the
+    BF16 control variate).  Returns the flagged fraction."""
     Nk = np.asarray(Nk, dtype=np.int64)
     rows_index = np.repeat(np.arange(len(rows)), Nk)
     rg, ro = gpu["rec"], orc["rec"]
@@ -67,6 +71,7 @@ def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3):
     babs = np.bincount(rows_index[~flag], weights=np.abs(ro["b_contrib"][~flag]),
                        minlength=len(rows))
     berr = np.abs(bg - bo)
-    bbad = berr > RTOL * babs + ATOL_RAW
+    extra = 0.0 if b_extra_tol is None else np.asarray(b_extra_tol)
+    bbad = berr > RTOL * babs + ATOL_RAW + extra
     assert not bbad.any(), f"b mismatch rows {np.nonzero(bbad)[0][:5]}: {bg[bbad]} vs {bo[bbad]}"
     return frac

@@ -1,0 +1,141 @@
+"""GPU tests of the learned control variate (Eq. 11, 37-39): the FP32
+training kernels and the BF16 tensor-core in-path evaluation of grad v_theta
+against the FP64 oracle, CV assembly parity, and the variance reduction the
+trained network buys over the plain estimator."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2301_05780_gb300 import pdds, workloads as W
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def u_exact(x, y):
+    return np.sin(np.pi * x) * np.cos(np.pi * y) + x * y
+
+
+def dev32(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def trained_theta():
+    """v_theta fitted by the library's own FP32 Adam kernels to samples of the
+    manufactured u of config 2 (Eq. 8's solution on [0,1]^2)."""
+    rng = np.random.default_rng(7)
+    xy = rng.uniform(0, 1, size=(8192, 2))
+    th = dev32(W.mlp_init())
+    hist = pdds.pdds_mlp_train(th, dev32(xy), dev32(u_exact(xy[:, 0], xy[:, 1])), steps=1500,
+                               lr=3e-3)
+    assert hist[-1] < 1e-2 * hist[0], (hist[0], hist[-1])
+    return th
+
+
+def test_mlp_loss_grad_matches_oracle(orc):
+    rng = np.random.default_rng(1)
+    th32 = W.mlp_init().astype(np.float32)
+    xy = rng.uniform(0, 1, size=(1000, 2)).astype(np.float32)
+    tgt = (np.sin(3 * xy[:, 0]) * xy[:, 1]).astype(np.float32)
+    loss_o, g_o = orc.mlp_loss_grad(th32.astype(np.float64), xy.astype(np.float64),
+                                    tgt.astype(np.float64))
+    loss, g = pdds.pdds_mlp_loss_grad(dev32(th32), dev32(xy), dev32(tgt))
+    assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g_o) <= 1e-4 * np.linalg.norm(g_o)
+
+
+def test_mlp_inpath_eval_matches_oracle(orc, trained_theta):
+    """The warp-batched BF16 MMA evaluation (also used inside the path kernel)
+    against the FP64 network: 1e-2 of the gradient scale (BF16 operands)."""
+    rng = np.random.default_rng(2)
+    xy = rng.uniform(0, 1, size=(1000 + 13, 2)).astype(np.float32)   # ragged last warp
+    th = trained_theta.cpu().numpy().astype(np.float64)
+    v, g = pdds.pdds_mlp_eval(trained_theta, dev32(xy))
+    v, g = v.cpu().numpy(), g.cpu().numpy()
+    vo = np.array([orc.mlp_value(th, *p) for p in xy.astype(np.float64)])
+    go = np.array([orc.mlp_grad_x(th, *p) for p in xy.astype(np.float64)])
+    scale = np.sqrt(np.mean(go ** 2))
+    assert np.abs(g - go).max() <= 2e-2 * scale, (np.abs(g - go).max(), scale)
+    assert np.abs(v - vo).max() <= 1e-2 * max(1.0, np.abs(vo).max())
+
+
+def test_trained_network_approximates_u(orc, trained_theta):
+    th = trained_theta.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(0, 1, size=(400, 2))
+    vo = np.array([orc.mlp_value(th, *p) for p in pts])
+    assert np.sqrt(np.mean((vo - u_exact(pts[:, 0], pts[:, 1])) ** 2)) < 0.05
+
+
+def _cv_workload(N, H=3, m=4):
+    w = W.config2().scaled(n_paths=N)
+    w.grid = dict(w.grid, Hx=H, Hy=H, m=m)
+    w.k_max = W.step_cap(w.grid, math.sqrt(2), w.dt)
+    return w
+
+
+def test_cv_assembly_parity_with_oracle(orc, trained_theta):
+    """Same streams, same theta: G as in the plain parity protocol; b within
+    1e-4 plus 2 % of sum |xi| (xi carries the BF16 network error)."""
+    w = _cv_workload(400)
+    P = pdds.Problem(w)
+    pdds.pdds_set_control_variate(P.ctx, trained_theta)
+    rec = P.records_buffer()
+    P.assemble(records=rec)
+    torch.cuda.synchronize()
+    assert pdds.pdds_stats(P.ctx)["device_error"] == 0
+    g = dict(row_ptr=P.row_ptr.cpu().numpy(), col=P.col.cpu().numpy(), val=P.val.cpu().numpy(),
+             b=P.b.cpu().numpy(), rec=pdds.records_to_numpy(rec))
+    O = orc.Problem(w.grid, w.coef_id, w.params)
+    _, _, _, rplain = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, records=True)
+    O.set_mlp(trained_theta.cpu().numpy().astype(np.float64))
+    val, b, _, rcv = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, records=True)
+    o = dict(row_ptr=O.row_ptr, col=O.col, val=val, b=b, rec=rcv)
+    xi = np.abs(rcv["b_contrib"] - rplain["b_contrib"])
+    n = P.n
+    xi_row = np.bincount(np.repeat(np.arange(n), w.n_paths), weights=xi, minlength=n)
+    assert xi_row.sum() > 0
+    parity.compare_rows(g, o, np.arange(n), np.full(n, w.n_paths), n,
+                        b_extra_tol=2e-2 * xi_row)
+
+
+def test_cv_reduces_variance_and_keeps_the_mean(trained_theta):
+    """Per-row sample variance of the path scores drops by > 10x with the
+    trained v_theta, and b moves by less than 4 standard errors."""
+    w = _cv_workload(4000, H=4, m=4)
+    P = pdds.Problem(w)
+    rec0 = P.records_buffer()
+    P.assemble(records=rec0)
+    b0 = P.b.cpu().numpy().copy()
+    pdds.pdds_set_control_variate(P.ctx, trained_theta)
+    rec1 = P.records_buffer()
+    P.assemble(records=rec1)
+    b1 = P.b.cpu().numpy()
+    torch.cuda.synchronize()
+    r0, r1 = pdds.records_to_numpy(rec0), pdds.records_to_numpy(rec1)
+    N, n = w.n_paths, P.n
+    # score of a path = its b contribution + sum_j w_j u_exact(x_j) (the G part)
+    xy = pdds.pdds_knot_coords(P.ctx)
+    ue = u_exact(xy[:, 0], xy[:, 1])
+
+    def scores(r):
+        s = r["b_contrib"].astype(np.float64).copy()
+        for c, wk in (("col_a", "w_a"), ("col_b", "w_b")):
+            m = r[c] >= 0
+            s[m] += r[wk][m] * ue[r[c][m]]
+        return s.reshape(n, N)
+
+    s0, s1 = scores(r0), scores(r1)
+    ratio = s0.var(axis=1).mean() / s1.var(axis=1).mean()
+    assert ratio > 10, ratio
+    se = np.sqrt(s0.var(axis=1) / N)
+    assert np.all(np.abs(b1 - b0) < 4 * se + 1e-12)
+    # detaching restores the plain estimator exactly (same streams)
+    pdds.pdds_set_control_variate(P.ctx, None)
+    P.assemble()
+    torch.cuda.synchronize()
+    assert np.allclose(P.b.cpu().numpy(), b0, rtol=1e-11, atol=1e-14)
