@@ -145,6 +145,17 @@ pdds_status pdds_set_launch(pdds_ctx* ctx, int32_t block, int32_t ctas_per_sm,
                             int32_t unit_paths, int32_t exit_batch);
 pdds_status pdds_get_launch(const pdds_ctx* ctx, int32_t* block, int32_t* ctas_per_sm,
                             int32_t* unit_paths, int32_t* exit_batch);
+/* Autotuner: times short assemblies of a sample of the knots (every 8th, at
+ * the full per-knot budget n_paths, time step dt) for every combination of
+ * block in {128, 256, 512}, unit_paths in {1024, 4096, 16384} and exit_batch
+ * in {2, 4, 8}, and keeps the fastest (ties to the first).  The launch shape
+ * only reorders floating-point additions, never the estimator.  Results are
+ * cached for the process per (device, coefficient set, control variate on/off,
+ * grid, n_paths); a cached shape is applied without timing.  Allocates and
+ * frees its own scratch and synchronizes the device. */
+pdds_status pdds_autotune(pdds_ctx* ctx, int64_t n_paths, double dt, uint64_t seed,
+                          void* cuda_stream);
+
 /* Bound, in seconds, on every device-side wait of the path kernel (a warp
  * waiting for the next work unit of its CTA).  When a wait runs out the kernel
  * stops taking work, returns, and pdds_stats reports PDDS_ETIMEOUT; the

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -240,6 +242,7 @@ struct pdds_ctx {
   // control variate (staged network image) and whether it is on
   void* d_mlp = nullptr;
   bool cv_on = false;
+  bool unit_domain_all = false;  // set by a batched launch: all its domains in [-1,1]^2
   std::vector<uint64_t> graph_key;
   pdds_stats_t st{};
   std::string err = "no error";
@@ -369,6 +372,14 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * (double)kmax);
   const bool cv = nprob == 1 && c->cv_on;
   kp.mlp = cv ? c->d_mlp : nullptr;
+  {
+    // all problems of the launch inside [-1, 1]^2 (problem 0 here, the batch
+    // caller checks the rest through c->unit_domain_all)
+    const pdds_grid& g = c->grid;
+    const bool u0 = std::fabs(g.x0) <= 1 && std::fabs(g.x1) <= 1 && std::fabs(g.y0) <= 1 &&
+                    std::fabs(g.y1) <= 1;
+    kp.unit_domain = (nprob == 1 ? u0 : c->unit_domain_all) ? 1 : 0;
+  }
   // the control-variate step is ~10x heavier: wait bounds scale with it
   if (cv && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * (double)kmax);
   // CV kernels keep the staged network at the start of dynamic shared memory
@@ -664,6 +675,87 @@ pdds_status pdds_set_wait_limit(pdds_ctx* c, double seconds) {
   return PDDS_OK;
 }
 
+pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed,
+                          void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "autotune: NULL context");
+  if (n_paths < 1 || !(dt > 0)) return fail(c, PDDS_EINVAL, "autotune: need n_paths >= 1, dt > 0");
+  // Cache key: device, coefficient set, control variate, grid shape, budget.
+  struct Key {
+    int dev, coef, cv, Hx, Hy, m, ext;
+    int64_t N;
+    bool operator<(const Key& o) const {
+      return std::tie(dev, coef, cv, Hx, Hy, m, ext, N) <
+             std::tie(o.dev, o.coef, o.cv, o.Hx, o.Hy, o.m, o.ext, o.N);
+    }
+  };
+  struct Shape { int block, unit, batch; };
+  static std::mutex mu;
+  static std::map<Key, Shape> cache;
+  const Key key{c->device, c->coef_id, c->cv_on ? 1 : 0, c->grid.Hx, c->grid.Hy, c->grid.m,
+                c->grid.ext, n_paths};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      c->block = it->second.block;
+      c->unit_paths = it->second.unit;
+      c->exit_batch = it->second.batch;
+      c->ctas_per_sm = 0;
+      return PDDS_OK;
+    }
+  }
+  (void)cudaGetLastError();
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = c->geo.n, nnz = c->geo.nnz;
+  // Sample every 8th knot (at least one) at the full budget; others get none.
+  std::vector<int64_t> Nh(n, 0);
+  for (int64_t k = 0; k < n; k += 8) Nh[k] = n_paths;
+  int64_t* dN = nullptr;
+  int32_t *rp = nullptr, *col = nullptr;
+  double *val = nullptr, *b = nullptr;
+  auto cleanup = [&] { cudaFree(dN); cudaFree(rp); cudaFree(col); cudaFree(val); cudaFree(b); };
+  if (dalloc(&dN, n) || dalloc(&rp, n + 1) || dalloc(&col, nnz) || dalloc(&val, nnz) ||
+      dalloc(&b, n)) {
+    cleanup();
+    return fail(c, PDDS_ENOMEM, "autotune: scratch allocation failed");
+  }
+  pdds_csr G{n, nnz, rp, col, val};
+  pdds_status st = PDDS_OK;
+  if (cudaMemcpy(dN, Nh.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    st = fail(c, PDDS_ECUDA, "autotune: upload failed");
+  const bool timing = c->timing;
+  const int blocks[] = {128, 256, 512};
+  const int units[] = {1024, 4096, 16384};
+  const int batches[] = {2, 4, 8};
+  Shape best{c->block, (int)c->unit_paths, c->exit_batch};
+  float best_ms = 1e30f;
+  c->timing = true;
+  c->ctas_per_sm = 0;
+  for (int bl : blocks)
+    for (int un : units)
+      for (int ba : batches) {
+        if (st != PDDS_OK) break;
+        if (c->cv_on && bl > 256) continue;
+        c->block = bl;
+        c->unit_paths = un;
+        c->exit_batch = ba;
+        st = assemble_impl(c, dN, 0, dt, seed, &G, b, nullptr, s);
+        if (st == PDDS_OK && c->st.path_kernel_ms < best_ms) {
+          best_ms = c->st.path_kernel_ms;
+          best = Shape{bl, un, ba};
+        }
+      }
+  c->timing = timing;
+  c->block = best.block;
+  c->unit_paths = best.unit;
+  c->exit_batch = best.batch;
+  cleanup();
+  if (st != PDDS_OK) return st;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = best;
+  return PDDS_OK;
+}
+
 pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_control_variate: NULL context");
   if (!theta) {
@@ -798,9 +890,12 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
   if (!(dt > 0)) return fail(c0, PDDS_EINVAL, "assemble_batch: dt must be > 0");
   int max_slots = 0, tw = 0, th = 0;
   int64_t kmax = 0;
+  bool unit_all = true;
   for (int i = 0; i < count; ++i) {
     pdds_ctx* c = ctxs[i];
     if (!c) return fail(c0, PDDS_EINVAL, "assemble_batch: NULL context in the list");
+    unit_all = unit_all && std::fabs(c->grid.x0) <= 1 && std::fabs(c->grid.x1) <= 1 &&
+               std::fabs(c->grid.y0) <= 1 && std::fabs(c->grid.y1) <= 1;
     if (c->coef_id != c0->coef_id)
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same coefficient set");
     if (c->device != c0->device)
@@ -815,6 +910,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
     th = std::max(th, c->tile_h);
     kmax = std::max(kmax, c->k_max > 0 ? c->k_max : default_kmax(c, dt));
   }
+  c0->unit_domain_all = unit_all;
   cudaStream_t s = (cudaStream_t)stream;
   // Graph key: everything the captured sequence depends on.
   std::vector<uint64_t> key = {(uint64_t)count, (uint64_t)Nu, (uint64_t)seed, (uint64_t)kmax,

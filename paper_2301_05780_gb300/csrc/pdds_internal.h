@@ -95,6 +95,8 @@ struct KParams {
   int32_t pad_;
   uint64_t wait_ns;        // bound on any device-side wait
   const void* mlp;         // staged control-variate network (MlpSmem), or nullptr
+  int32_t unit_domain;     // every problem's Omega lies in [-1, 1]^2 (no trig reduction)
+  int32_t pad2_;
 };
 
 // Launchers implemented in the .cu files (host-callable).

@@ -54,16 +54,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Box-Muller (1958) on two 32-bit words: u = (w + 1/2) 2^-32,
-// rho = sqrt(-2 ln u_a), theta = 2 pi u_b (reduced to [-pi, pi) before the
-// hardware sine/cosine, which is exact in value).
+// rho = sqrt(-2 ln u_a), theta = 2 pi u_b (reduced to [-pi, pi] before the
+// hardware sine/cosine, which is exact in value).  u_a keeps all 32 bits (its
+// logarithm decides the tail of rho); u_b is built from its top 23 bits,
+// (w_b >> 9 + 1/2) 2^-23, which moves theta by at most 2^-23 pi.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
   const float s32 = 2.3283064365386963e-10f;  // 2^-32
   const float ua = fmaf(__uint2float_rn(a), s32, 0.5f * s32);
-  const float ub = fmaf(__uint2float_rn(b), s32, 0.5f * s32);
-  const float t = fmaxf(-2.0f * __logf(ua), 1e-30f);
-  const float rho = t * rsqrtf(t);
-  const float r = ub - (ub >= 0.5f ? 1.0f : 0.0f);
+  const float ub = __uint_as_float(0x3f800000u | (b >> 9)) - 0.99999994039535522f;
+  const float rho = sqrt_approx(-1.38629436111989061f * lg2_approx(ua));  // -2 ln u_a
+  const float r = ub - rintf(ub);
   float sn, cs;
   __sincosf(kTwoPi * r, &sn, &cs);
   z0 = rho * cs;
@@ -207,17 +219,22 @@ __device__ __forceinline__ float bilinear(const float* T, int w, float fx, float
 // point relative to the knot (used by the tabulated set).
 template <int COEF>
 __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const float* tc,
-                                       float x, float y, float xr, float yr, float& s, float& dx,
-                                       float& dy, float& c, float& f) {
+                                       float x, float y, float xr, float yr, bool unit_domain,
+                                       float& s, float& dx, float& dy, float& c, float& f) {
   if constexpr (COEF == PDDS_COEF_LAPLACE_EXPSIN) {
     s = 1.41421356237309505f; dx = 0.f; dy = 0.f; c = 0.f; f = 0.f;
   } else if constexpr (COEF == PDDS_COEF_MANUFACTURED) {
     // u = sin(pi x) cos(pi y) + x y, Lap u = -2 pi^2 sin(pi x) cos(pi y),
     // d = (sin 2 pi y, cos 2 pi x), c = -(1 + x^2), f = Lap u + d.grad u + c u.
     float sx, cx, sy, cy;
-    sincos_2pi(0.5f * x, sx, cx);
-    sincos_2pi(0.5f * y, sy, cy);
     const float pi = 3.14159265358979324f;
+    if (unit_domain) {  // |x|, |y| <= 1: pi x is already within [-pi, pi]
+      __sincosf(pi * x, &sx, &cx);
+      __sincosf(pi * y, &sy, &cy);
+    } else {
+      sincos_2pi(0.5f * x, sx, cx);
+      sincos_2pi(0.5f * y, sy, cy);
+    }
     const float u = fmaf(sx, cy, x * y);
     const float ux = fmaf(pi * cx, cy, y);
     const float uy = fmaf(-pi * sx, sy, x);
@@ -252,6 +269,10 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
 template <int COEF>
 __host__ __device__ constexpr bool has_potential() {  // c or f may be nonzero
   return COEF != PDDS_COEF_LAPLACE_EXPSIN;
+}
+template <int COEF>
+__host__ __device__ constexpr bool has_drift() {  // d may be nonzero
+  return COEF == PDDS_COEF_MANUFACTURED || COEF == PDDS_COEF_CONSTANT;
 }
 
 __device__ __forceinline__ const ProbDesc& prob_desc(const KParams& P, int i) {
@@ -555,7 +576,8 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
           if (go && !exited) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
-            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, s, ddx, ddy, c, f);
+            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
+                         s, ddx, ddy, c, f);
             const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
             float Yw = 1.0f;
             if constexpr (has_potential<COEF>()) {
@@ -564,8 +586,9 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
               Sx = fmaf(c, h, Sx);
             }
             XI = fmaf(-Yw * s, fmaf(gx, dWx, gy * dWy), XI);
-            X += fmaf(ddx, h, s * dWx);
-            Y += fmaf(ddy, h, s * dWy);
+            const float ssh = s * sqh;
+            X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
+            Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
             ++n;
             exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
             if (!exited && n >= kmax) { exited = true; trunc = true; }
@@ -582,15 +605,22 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
           if (!exited) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
-            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, s, ddx, ddy, c, f);
-            const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
+            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
+                         s, ddx, ddy, c, f);
             if constexpr (has_potential<COEF>()) {
               const float Yw = __expf(Sx);
               Z = fmaf(-f * Yw, h, Z);  // dZ = -f Y dt
               Sx = fmaf(c, h, Sx);      // dY = c Y dt, Y = exp(S)
             }
-            X += fmaf(ddx, h, s * dWx);  // dX = d dt + s dW
-            Y += fmaf(ddy, h, s * dWy);
+            // dX = d dt + s dW with dW = sqrt(h) z: s sqrt(h) once, then two FMAs
+            const float ssh = s * sqh;
+            if constexpr (has_drift<COEF>()) {
+              X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
+              Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
+            } else {
+              X = fmaf(ssh, z[2 * half], X);
+              Y = fmaf(ssh, z[2 * half + 1], Y);
+            }
             ++n;
             exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
             if (!exited && n >= kmax) { exited = true; trunc = true; }

@@ -72,6 +72,7 @@ _SIGS = {
     "pdds_get_launch": (C.c_int, [_P, _P, _P, _P, _P]),
     "pdds_set_timing": (C.c_int, [_P, C.c_int32]),
     "pdds_set_wait_limit": (C.c_int, [_P, C.c_double]),
+    "pdds_autotune": (C.c_int, [_P, C.c_int64, C.c_double, C.c_uint64, _P]),
     "pdds_assemble": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P]),
     "pdds_assemble_records": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P,
                                         _P]),
@@ -189,6 +190,14 @@ def pdds_get_launch(ctx):
     v = [C.c_int32() for _ in range(4)]
     _check(lib().pdds_get_launch(ctx, *[C.byref(x) for x in v]), ctx)
     return tuple(x.value for x in v)
+
+
+def pdds_autotune(ctx, n_paths, dt, seed=0, stream=None):
+    """Times candidate launch shapes on a knot sample and keeps the fastest;
+    returns (block, ctas_per_sm, unit_paths, exit_batch)."""
+    _check(lib().pdds_autotune(ctx, int(n_paths), float(dt), C.c_uint64(int(seed) % 2**64),
+                               _stream(stream)), ctx)
+    return pdds_get_launch(ctx)
 
 
 def pdds_set_wait_limit(ctx, seconds: float):

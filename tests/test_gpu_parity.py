@@ -170,6 +170,25 @@ def test_launch_shapes_give_the_same_sums(launch):
     assert a["stats"]["path_steps"] == b["stats"]["path_steps"]
 
 
+def test_autotune_picks_a_candidate_and_keeps_the_estimator():
+    """The autotuner only changes the launch shape: the shape is one of its
+    candidates, G and b are unchanged (to FP64 summation order), and a second
+    call for the same problem is served from the cache."""
+    import time
+    w = W.config2().scaled(n_paths=2000)
+    before = run_gpu(w, records=False)
+    P = pdds.Problem(w)
+    block, per_sm, unit, batch = pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed)
+    assert block in (128, 256, 512) and unit in (1024, 4096, 16384) and batch in (2, 4, 8)
+    P.assemble()
+    torch.cuda.synchronize()
+    assert np.allclose(P.val.cpu().numpy(), before["val"], rtol=1e-11, atol=1e-14)
+    assert np.allclose(P.b.cpu().numpy(), before["b"], rtol=1e-11, atol=1e-14)
+    t0 = time.perf_counter()
+    assert pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed) == (block, per_sm, unit, batch)
+    assert time.perf_counter() - t0 < 0.05
+
+
 # ------------------------------------------------------------ tables (TMA)
 def test_tabulated_small_full_parity(orc):
     """TABLE coefficients through TMA tiles: 4x4 grid, 16 knot intervals per
