@@ -29,6 +29,11 @@ COEF_MANUFACTURED = 1
 COEF_VARSIGMA = 2
 COEF_TABLE = 3
 COEF_CONSTANT = 4
+COEF_POISSON_E1 = 5
+SCHEME_EM = 0
+SCHEME_GM = 1
+GM_SHIFT = 0.5826
+CAL_NMOM = 8
 MLP_NPARAM = 64 * 2 + 64 + 64 * 64 + 64 + 64 + 1
 
 
@@ -63,6 +68,18 @@ RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side", "<i4"), ("flags", "<i4"),
                          ("w_a", "<f8"), ("w_b", "<f8"), ("b_contrib", "<f8"), ("Y", "<f8")])
 
 
+CAL_RECORD_DTYPE = np.dtype([("steps_gm", "<i4"), ("side_gm", "<i4"), ("flags_gm", "<i4"),
+                             ("steps_em", "<i4"), ("side_em", "<i4"), ("flags_em", "<i4"),
+                             ("phi_gm", "<f8"), ("phi_em", "<f8"), ("xi_gm", "<f8"),
+                             ("pad_", "<f8")])
+
+
+class Run(C.Structure):
+    _fields_ = [("n_per_knot", C.c_void_p), ("n_paths", C.c_int64), ("dt", C.c_double),
+                ("h_per_knot", C.c_void_p), ("k_max", C.c_int64), ("seed", C.c_uint64),
+                ("tag_word", C.c_uint32), ("scheme", C.c_int32)]
+
+
 def lib():
     global _LIB
     with _LOCK:
@@ -76,6 +93,10 @@ def lib():
             L.orc_geometry.argtypes = [P, P, P, P]
             L.orc_assemble.argtypes = [P, P, P, C.c_int64, C.c_double, C.c_uint64, C.c_uint32,
                                        C.c_int64, P, C.c_int32, C.c_int32, P, P, P, P]
+            L.orc_assemble_ex.argtypes = [P, P, P, P, C.c_int32, C.c_int32, P, P, P, P]
+            L.orc_calibrate.argtypes = [P, P, P, P, P, C.c_int32, C.c_int32, P, P, P]
+            L.orc_plan.argtypes = [C.c_int64, P, C.c_double, C.c_double, C.c_double, C.c_int64,
+                                   P, P, P]
             L.orc_finalize_rows.argtypes = [P, P, P, P, C.c_int64, P, C.c_int32, P, P]
             L.orc_coeffs_eval.argtypes = [P, P, C.c_double, C.c_double, P, P, P, P, P]
             L.orc_boundary_g.argtypes = [P, C.c_double, C.c_double]
@@ -139,16 +160,7 @@ class Problem:
             assert self._mlp.size == MLP_NPARAM
             self.coef.mlp = self._mlp.ctypes.data
 
-    def assemble(self, n_paths, dt, seed, k_max, rows=None, threads=None, tag=0,
-                 records=False, finalize=True):
-        """Rows of G (CSR values in this object's pattern) and b (Eq. 24-25).
-
-        n_paths is an int (all knots) or an int64 array of length n.
-        Returns (val, b, stats, records-or-None)."""
-        L = lib()
-        if rows is None:
-            rows = np.arange(self.n, dtype=np.int32)
-        rows = np.ascontiguousarray(rows, dtype=np.int32)
+    def _run(self, n_paths, dt, seed, k_max, tag, scheme, h_per_knot):
         per = None
         N = 0
         if np.ndim(n_paths) == 0:
@@ -156,6 +168,26 @@ class Problem:
         else:
             per = np.ascontiguousarray(n_paths, dtype=np.int64)
             assert per.size == self.n
+        h = None
+        if h_per_knot is not None:
+            h = np.ascontiguousarray(h_per_knot, dtype=np.float64)
+            assert h.size == self.n
+        run = Run(_p(per), N, float(dt), _p(h), int(k_max), int(seed) & (2**64 - 1),
+                  int(tag) & 0xffffffff, int(scheme))
+        return run, per, N, h
+
+    def assemble(self, n_paths, dt, seed, k_max, rows=None, threads=None, tag=0,
+                 records=False, finalize=True, scheme=SCHEME_EM, h_per_knot=None):
+        """Rows of G (CSR values in this object's pattern) and b (Eq. 24-25).
+
+        n_paths is an int (all knots) or an int64 array of length n; h_per_knot
+        (optional, length n) gives each knot its own step, dt is then only the
+        step at which k_max is counted.  Returns (val, b, stats, records-or-None)."""
+        L = lib()
+        if rows is None:
+            rows = np.arange(self.n, dtype=np.int32)
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, scheme, h_per_knot)
         threads = int(threads or os.cpu_count() or 1)
         val = np.zeros(max(self.nnz, 1))[: self.nnz]
         b = np.zeros(self.n)
@@ -164,15 +196,39 @@ class Problem:
         if records:
             total = int(per[rows].sum()) if per is not None else N * rows.size
             rec = np.zeros(total, dtype=RECORD_DTYPE)
-        rc = L.orc_assemble(C.byref(self.grid), C.byref(self.coef), _p(per), N, float(dt),
-                            C.c_uint64(int(seed) & (2**64 - 1)), C.c_uint32(int(tag)), int(k_max),
-                            _p(rows), rows.size, threads, _p(val), _p(b), _p(rec), _p(stats))
+        rc = L.orc_assemble_ex(C.byref(self.grid), C.byref(self.coef), C.byref(run), _p(rows),
+                               rows.size, threads, _p(val), _p(b), _p(rec), _p(stats))
         if rc != 0:
             raise ValueError(f"oracle assemble failed ({rc})")
         if finalize:
             L.orc_finalize_rows(C.byref(self.grid), _p(self.row_ptr), _p(self.col), _p(per), N,
                                 _p(rows), rows.size, _p(val), _p(b))
         return val, b, stats, rec
+
+    def calibrate(self, u0, n_paths, dt, seed, k_max, rows=None, threads=None, tag=0,
+                  records=False, h_per_knot=None):
+        """Mixed GM/EM calibration run (Sec. 4.1) with the nodal u0 as patch data.
+
+        Returns (moments [len(rows), CAL_NMOM], stats, records-or-None)."""
+        L = lib()
+        if rows is None:
+            rows = np.arange(self.n, dtype=np.int32)
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        assert u0.size == self.n
+        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, SCHEME_EM, h_per_knot)
+        threads = int(threads or os.cpu_count() or 1)
+        mom = np.zeros((rows.size, CAL_NMOM))
+        stats = np.zeros(3, dtype=np.int64)
+        rec = None
+        if records:
+            total = int(per[rows].sum()) if per is not None else N * rows.size
+            rec = np.zeros(total, dtype=CAL_RECORD_DTYPE)
+        rc = L.orc_calibrate(C.byref(self.grid), C.byref(self.coef), C.byref(run), _p(u0),
+                             _p(rows), rows.size, threads, _p(mom), _p(rec), _p(stats))
+        if rc != 0:
+            raise ValueError(f"oracle calibrate failed ({rc})")
+        return mom, stats, rec
 
     def dense(self, val):
         A = np.zeros((self.n, self.n))
@@ -248,6 +304,18 @@ def mlp_loss_grad(theta, xy, target):
     g = np.zeros(MLP_NPARAM)
     loss = lib().orc_mlp_loss_grad(_p(theta), _p(xy), _p(target), target.size, _p(g))
     return loss, g
+
+
+def plan(moments, eps, h0, h0p, n_job):
+    """Eq. 40-41: per-knot (h_i, N_i) and diagnostics (gap, var, rho^2)."""
+    mom = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1, CAL_NMOM)
+    n = mom.shape[0]
+    h = np.zeros(n)
+    N = np.zeros(n, dtype=np.int64)
+    diag = np.zeros((n, 3))
+    lib().orc_plan(n, _p(mom), float(eps), float(h0), float(h0p), int(n_job), _p(h), _p(N),
+                   _p(diag))
+    return h, N, diag
 
 
 def adam_step(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

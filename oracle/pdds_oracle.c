@@ -227,6 +227,35 @@ static double table_bilinear(const orc_grid* g, const float* T, int nx, int ny, 
   return (1 - tx) * (1 - ty) * v00 + tx * (1 - ty) * v10 + (1 - tx) * ty * v01 + tx * ty * v11;
 }
 
+/* Eq. 43: u = 3 + sin(r)/3 + tanh(q)/3 with r = sqrt(1 + x^2/100 + y^2/50) and
+ * q = sin(3x/25 + y/20) + sin(x/20 - 3y/25). */
+static double e1_u(double x, double y) {
+  double r = sqrt(1.0 + x * x / 100.0 + y * y / 50.0);
+  double q = sin(3.0 * x / 25.0 + y / 20.0) + sin(x / 20.0 - 3.0 * y / 25.0);
+  return 3.0 + sin(r) / 3.0 + tanh(q) / 3.0;
+}
+
+/* Lap u of Eq. 43, by the chain rule:
+ *   Lap sin r = cos r Lap r - sin r |grad r|^2,  |grad r|^2 = G / r^2,
+ *   Lap r = (1/100 + 1/50) / r - G / r^3,         G = x^2/100^2 + y^2/50^2;
+ *   Lap tanh q = (1 - T^2) Lap q - 2 T (1 - T^2) |grad q|^2,  T = tanh q,
+ *   Lap q = -((3/25)^2 + (1/20)^2) q,
+ *   grad q = ((3/25) cos a + (1/20) cos b, (1/20) cos a - (3/25) cos b). */
+static double e1_laplacian(double x, double y) {
+  double r = sqrt(1.0 + x * x / 100.0 + y * y / 50.0);
+  double G = x * x / 1.0e4 + y * y / 2.5e3;
+  double lap_r = (1.0 / 100.0 + 1.0 / 50.0) / r - G / (r * r * r);
+  double lap_sin = cos(r) * lap_r - sin(r) * G / (r * r);
+  double a = 3.0 * x / 25.0 + y / 20.0, bb = x / 20.0 - 3.0 * y / 25.0;
+  double q = sin(a) + sin(bb);
+  double qx = 3.0 / 25.0 * cos(a) + cos(bb) / 20.0;
+  double qy = cos(a) / 20.0 - 3.0 / 25.0 * cos(bb);
+  double T = tanh(q);
+  double lap_q = -((3.0 / 25.0) * (3.0 / 25.0) + (1.0 / 20.0) * (1.0 / 20.0)) * q;
+  double lap_tanh = (1.0 - T * T) * lap_q - 2.0 * T * (1.0 - T * T) * (qx * qx + qy * qy);
+  return (lap_sin + lap_tanh) / 3.0;
+}
+
 void orc_coeffs_eval(const orc_grid* g, const orc_coeffs* cf, double x, double y,
                      double* s, double* dx, double* dy, double* c, double* f) {
   const double pi = M_PI;
@@ -261,6 +290,11 @@ void orc_coeffs_eval(const orc_grid* g, const orc_coeffs* cf, double x, double y
     *c = table_bilinear(g, cf->c_tab, cf->tab_nx, cf->tab_ny, x, y);
     *dx = 0; *dy = 0; *f = cf->params[0];
     break;
+  case ORC_COEF_POISSON_E1:
+    /* Eq. 42 reads Lap u = f; with s = sqrt2 the generator (s^2/2) Lap is Lap,
+     * so f is Eq. 42's right-hand side, Lap of the u of Eq. 43. */
+    *s = sqrt(2.0); *dx = 0; *dy = 0; *c = 0; *f = e1_laplacian(x, y);
+    break;
   default: /* ORC_COEF_CONSTANT */
     *s = cf->params[0]; *dx = cf->params[1]; *dy = cf->params[2];
     *c = cf->params[3]; *f = cf->params[4];
@@ -275,6 +309,7 @@ double orc_boundary_g(const orc_coeffs* cf, double x, double y) {
   case ORC_COEF_MANUFACTURED:   return sin(pi * x) * cos(pi * y) + x * y;
   case ORC_COEF_VARSIGMA:       return exp(x / 4.0) * cos(y / 2.0);
   case ORC_COEF_TABLE:          return cf->params[1];
+  case ORC_COEF_POISSON_E1:     return e1_u(x, y);
   default:                      return cf->params[5];
   }
 }
@@ -378,7 +413,8 @@ void orc_adam_step(double* th, const double* g, double* m, double* v, int64_t t,
 typedef struct {
   const geom_t* G;
   const orc_coeffs* cf;
-  double h, sqh;
+  double dt;                 /* reference step (the step cap k_max is given at dt) */
+  const double* h_per_knot;  /* per-knot steps h_k, or NULL for dt everywhere      */
   uint32_t key[2];
   uint32_t tag;
   int64_t k_max;
@@ -388,50 +424,56 @@ typedef struct {
   int steps, side, flags;
   int col[2];          /* unknown-knot columns, -1 if none */
   double w[2];         /* Y * interpolation weight for col[]  */
-  double bsum;         /* everything that goes to b           */
+  double bsum;         /* everything that goes to b (Z + xi + Dirichlet terms) */
   double Y;
+  double xi;           /* the control-variate integral alone (0 without one) */
 } path_out_t;
 
-static void simulate_path(const sim_t* S, int k, int64_t p, path_out_t* out) {
+typedef struct { double xlo, xhi, ylo, yhi; } box_t;
+
+/* Step of knot k and its step cap: the cap covers the same time horizon as
+ * k_max steps of dt, i.e. ceil(k_max dt / h_k) steps. */
+static double knot_h(const sim_t* S, int k) {
+  return S->h_per_knot ? S->h_per_knot[k] : S->dt;
+}
+static int64_t knot_cap(const sim_t* S, double h) {
+  if (h == S->dt) return S->k_max;
+  double c = ceil((double)S->k_max * S->dt / h);
+  return c < 1.0 ? 1 : (int64_t)c;
+}
+
+/* Gobet-Menozzi shift (Sec. 2.3): every side of the patch moves inwards by
+ * 0.5826 |sigma(P) N| sqrt(h), with P the normal projection of the current
+ * point on that side (kept on the closed side) and N its normal.  With
+ * sigma = s I this is 0.5826 |s(P)| sqrt(h). */
+static void gm_shifts(const sim_t* S, const box_t* B, double X, double Yp, double h,
+                      double shift[4]) {
+  double cx = X < B->xlo ? B->xlo : (X > B->xhi ? B->xhi : X);
+  double cy = Yp < B->ylo ? B->ylo : (Yp > B->yhi ? B->yhi : Yp);
+  const double px[4] = {B->xhi, cx, B->xlo, cx};
+  const double py[4] = {cy, B->yhi, cy, B->ylo};
+  for (int o = 0; o < 4; ++o) {
+    double s, dxv, dyv, c, f;
+    orc_coeffs_eval(&S->G->g, S->cf, px[o], py[o], &s, &dxv, &dyv, &c, &f);
+    shift[o] = ORC_GM_SHIFT * fabs(s) * sqrt(h);
+  }
+}
+
+/* Exit resolution (Eq. 22-25, corner rule of Sec. 3.3) of the state
+ * (X, Yp, Y = exp(Sacc), Z, xi) after n steps.  The exit side is the side
+ * with the smallest positive overshoot past its line moved inwards by
+ * shift[o] (all zero for naive EM; ties E < N < W < S); a truncated path that
+ * is inside every moved line goes to the nearest one.  The exit point is the
+ * normal projection on the side's true line. */
+static void resolve_exit(const sim_t* S, const patch_t* P, const box_t* B, double X, double Yp,
+                         double Sacc, double Z, double xi, int truncated, int64_t n,
+                         const double shift[4], path_out_t* out) {
   const geom_t* G = S->G;
   const orc_grid* g = &G->g;
-  patch_t P; make_patch(G, k, &P);
-  double xlo = g->x0 + P.ilo * G->dx, xhi = g->x0 + P.ihi * G->dx;
-  double ylo = g->y0 + P.jlo * G->dy, yhi = g->y0 + P.jhi * G->dy;
-  double X = g->x0 + G->ki[k] * G->dx, Yp = g->y0 + G->kj[k] * G->dy;
-  double Sacc = 0.0, Z = 0.0, xi = 0.0;   /* Y = exp(S) */
-  int64_t n = 0;
-  int truncated = 0;
-  double z[4] = {0, 0, 0, 0};
-  for (;;) {
-    if ((n & 1) == 0) {
-      /* One Philox call per two steps: counter (step pair, path, knot, tag). */
-      uint32_t ctr[4] = {(uint32_t)(n >> 1), (uint32_t)p, (uint32_t)k, S->tag}, r[4];
-      orc_philox4x32_10(ctr, S->key, r);
-      orc_box_muller(r[0], r[1], &z[0], &z[1]);
-      orc_box_muller(r[2], r[3], &z[2], &z[3]);
-    }
-    double zx = z[(n & 1) * 2], zy = z[(n & 1) * 2 + 1];
-    double s, dxv, dyv, c, f;
-    orc_coeffs_eval(g, S->cf, X, Yp, &s, &dxv, &dyv, &c, &f);
-    double Yw = exp(Sacc);
-    double dWx = S->sqh * zx, dWy = S->sqh * zy;
-    Z -= f * Yw * S->h;                                  /* dZ = -f Y dt      */
-    if (S->cf->mlp) {                                    /* dxi = -Y F . dW   */
-      double gx, gy;
-      orc_mlp_grad_x(S->cf->mlp, X, Yp, &gx, &gy);
-      xi -= Yw * s * (gx * dWx + gy * dWy);              /* F = sigma^T grad v */
-    }
-    Sacc += c * S->h;                                    /* dY = c Y dt       */
-    X += dxv * S->h + s * dWx;                           /* dX = d dt + s dW  */
-    Yp += dyv * S->h + s * dWy;
-    ++n;
-    if (X > xhi || X < xlo || Yp > yhi || Yp < ylo) break;   /* left closed patch */
-    if (n >= S->k_max) { truncated = 1; break; }
-  }
   double Yk = exp(Sacc);
-  /* Signed overshoot past each side, E N W S. */
-  double ov[4] = {X - xhi, Yp - yhi, xlo - X, ylo - Yp};
+  /* Signed overshoot past each (moved) side, E N W S. */
+  double ov[4] = {X - B->xhi + shift[0], Yp - B->yhi + shift[1], B->xlo - X + shift[2],
+                  B->ylo - Yp + shift[3]};
   int side = -1;
   for (int o = 0; o < 4; ++o)          /* smallest positive overshoot */
     if (ov[o] > 0 && (side < 0 || ov[o] < ov[side])) side = o;
@@ -445,11 +487,12 @@ static void simulate_path(const sim_t* S, int k, int64_t p, path_out_t* out) {
   out->col[0] = out->col[1] = -1;
   out->w[0] = out->w[1] = 0;
   out->Y = Yk;
+  out->xi = xi;
   double bsum = Z + xi;
   int vertical = (side == 0 || side == 2);
-  double line_xy = vertical ? (side == 0 ? xhi : xlo) : (side == 1 ? yhi : ylo);
+  double line_xy = vertical ? (side == 0 ? B->xhi : B->xlo) : (side == 1 ? B->yhi : B->ylo);
   double along = vertical ? Yp : X;
-  if (P.dirichlet[side]) {
+  if (P->dirichlet[side]) {
     /* Exit on the boundary of Omega: score g(P) Y (Eq. 25), P projected
      * normally and kept in the closure of Omega. */
     double lo = vertical ? g->y0 : g->x0, hi = vertical ? g->y1 : g->x1;
@@ -463,16 +506,16 @@ static void simulate_path(const sim_t* S, int k, int64_t p, path_out_t* out) {
     double origin = vertical ? g->y0 : g->x0, step = vertical ? G->dy : G->dx;
     int lmax = vertical ? G->LY : G->LX;
     double s = (along - origin) / step;
-    if (s < P.a[side]) { s = P.a[side]; out->flags |= 2; }
-    if (s > P.b[side]) { s = P.b[side]; out->flags |= 2; }
+    if (s < P->a[side]) { s = P->a[side]; out->flags |= 2; }
+    if (s > P->b[side]) { s = P->b[side]; out->flags |= 2; }
     int t = (int)floor(s);
-    if (t >= P.b[side]) t = P.b[side] - 1;
+    if (t >= P->b[side]) t = P->b[side] - 1;
     double lam = s - t;
     double w[2] = {1.0 - lam, lam};
     for (int q = 0; q < 2; ++q) {
       int tl = t + q;
-      int i = vertical ? P.line[side] : tl;
-      int j = vertical ? tl : P.line[side];
+      int i = vertical ? P->line[side] : tl;
+      int j = vertical ? tl : P->line[side];
       if (tl == 0 || tl == lmax) {
         /* Stencil end on the boundary of Omega: known value g there. */
         bsum += Yk * w[q] * orc_boundary_g(S->cf, g->x0 + i * G->dx, g->y0 + j * G->dy);
@@ -485,12 +528,86 @@ static void simulate_path(const sim_t* S, int k, int64_t p, path_out_t* out) {
   out->bsum = bsum;
 }
 
+/* One Feynman-Kac path inside the patch of knot k (Eq. 9, Euler-Maruyama with
+ * the knot's step h_k).  mode bit 0 asks for the naive exit (first step
+ * outside the closed patch), bit 1 for the Gobet-Menozzi exit (first step
+ * outside the patch with its sides moved inwards, Sec. 2.3).  With both bits
+ * the path is the "mixed GM/EM" trajectory of Sec. 4.1: after the GM exit it
+ * simply goes on until the naive exit, so both scores come from one path. */
+static void simulate(const sim_t* S, int k, int64_t p, int mode, path_out_t* em, path_out_t* gm) {
+  const geom_t* G = S->G;
+  const orc_grid* g = &G->g;
+  patch_t P; make_patch(G, k, &P);
+  box_t B = {g->x0 + P.ilo * G->dx, g->x0 + P.ihi * G->dx,
+             g->y0 + P.jlo * G->dy, g->y0 + P.jhi * G->dy};
+  const double h = knot_h(S, k), sqh = sqrt(h);
+  const int64_t cap = knot_cap(S, h);
+  const double zero[4] = {0, 0, 0, 0};
+  double X = g->x0 + G->ki[k] * G->dx, Yp = g->y0 + G->kj[k] * G->dy;
+  double Sacc = 0.0, Z = 0.0, xi = 0.0;   /* Y = exp(S) */
+  int64_t n = 0;
+  int need_em = mode & 1, need_gm = (mode >> 1) & 1;
+  double z[4] = {0, 0, 0, 0};
+  for (;;) {
+    if ((n & 1) == 0) {
+      /* One Philox call per two steps: counter (step pair, path, knot, tag). */
+      uint32_t ctr[4] = {(uint32_t)(n >> 1), (uint32_t)p, (uint32_t)k, S->tag}, r[4];
+      orc_philox4x32_10(ctr, S->key, r);
+      orc_box_muller(r[0], r[1], &z[0], &z[1]);
+      orc_box_muller(r[2], r[3], &z[2], &z[3]);
+    }
+    double zx = z[(n & 1) * 2], zy = z[(n & 1) * 2 + 1];
+    double s, dxv, dyv, c, f;
+    orc_coeffs_eval(g, S->cf, X, Yp, &s, &dxv, &dyv, &c, &f);
+    double Yw = exp(Sacc);
+    double dWx = sqh * zx, dWy = sqh * zy;
+    Z -= f * Yw * h;                                     /* dZ = -f Y dt      */
+    if (S->cf->mlp) {                                    /* dxi = -Y F . dW   */
+      double gx, gy;
+      orc_mlp_grad_x(S->cf->mlp, X, Yp, &gx, &gy);
+      xi -= Yw * s * (gx * dWx + gy * dWy);              /* F = sigma^T grad v */
+    }
+    Sacc += c * h;                                       /* dY = c Y dt       */
+    X += dxv * h + s * dWx;                              /* dX = d dt + s dW  */
+    Yp += dyv * h + s * dWy;
+    ++n;
+    if (need_gm) {                                       /* left the moved patch */
+      double sh[4];
+      gm_shifts(S, &B, X, Yp, h, sh);
+      if (X > B.xhi - sh[0] || Yp > B.yhi - sh[1] || X < B.xlo + sh[2] || Yp < B.ylo + sh[3]) {
+        resolve_exit(S, &P, &B, X, Yp, Sacc, Z, xi, 0, n, sh, gm);
+        need_gm = 0;
+      }
+    }
+    if (need_em && (X > B.xhi || X < B.xlo || Yp > B.yhi || Yp < B.ylo)) {  /* left closed patch */
+      resolve_exit(S, &P, &B, X, Yp, Sacc, Z, xi, 0, n, zero, em);
+      need_em = 0;
+    }
+    if (!need_em && !need_gm) break;
+    if (n >= cap) {                                      /* truncated */
+      if (need_gm) {
+        double sh[4];
+        gm_shifts(S, &B, X, Yp, h, sh);
+        resolve_exit(S, &P, &B, X, Yp, Sacc, Z, xi, 1, n, sh, gm);
+      }
+      if (need_em) resolve_exit(S, &P, &B, X, Yp, Sacc, Z, xi, 1, n, zero, em);
+      break;
+    }
+  }
+}
+
 /* ========================================================================= *
  * Row assembly (Eq. 24-25).  Raw sums: val holds sum_p Y w for each column,   *
  * b holds sum_p of the b contributions; orc_finalize_rows divides by N_k.     *
  * ========================================================================= */
-typedef struct {
+typedef struct job_s job_t;
+struct job_s {
   sim_t S;
+  int scheme;
+  void (*row_fn)(job_t*, int, int64_t*);
+  const double* u0;          /* calibration: nodal warm-up solution */
+  double* moments;           /* calibration: [nrows][ORC_CAL_NMOM] */
+  orc_cal_record* cal_records;
   const int64_t* n_per_knot;
   int64_t n_paths;
   const int32_t* rows;
@@ -502,7 +619,7 @@ typedef struct {
   int next;                    /* shared row counter */
   pthread_mutex_t mu;
   int64_t stats[3];
-} job_t;
+};
 
 static int64_t paths_of(const job_t* J, int k) {
   return J->n_per_knot ? J->n_per_knot[k] : J->n_paths;
@@ -518,7 +635,8 @@ static void assemble_row(job_t* J, int r, int64_t* st) {
   double bacc = 0.0;
   for (int64_t p = 0; p < N; ++p) {
     path_out_t o;
-    simulate_path(&J->S, k, p, &o);
+    if (J->scheme == ORC_SCHEME_GM) simulate(&J->S, k, p, 2, NULL, &o);
+    else simulate(&J->S, k, p, 1, &o, NULL);
     st[0] += o.steps;
     st[1] += (o.flags & 1) ? 1 : 0;
     st[2] += (o.flags & 2) ? 1 : 0;
@@ -554,7 +672,7 @@ static void* worker(void* arg) {
     int r = J->next++;
     pthread_mutex_unlock(&J->mu);
     if (r >= J->nrows) break;
-    assemble_row(J, r, st);
+    J->row_fn(J, r, st);
   }
   pthread_mutex_lock(&J->mu);
   for (int i = 0; i < 3; ++i) J->stats[i] += st[i];
@@ -562,41 +680,175 @@ static void* worker(void* arg) {
   return NULL;
 }
 
+/* Common set-up of a threaded run over the requested rows; returns 0 or an
+ * error code (invalid step, cap or row). */
+static int job_begin(job_t* J, geom_t* G, const orc_grid* g, const orc_coeffs* cf,
+                     const orc_run* run, const int32_t* rows, int32_t nrows) {
+  if (!(run->dt > 0) || run->k_max < 1) return -1;
+  if (geom_build(g, G, 1)) return -1;
+  for (int r = 0; r < nrows; ++r)
+    if (rows[r] < 0 || rows[r] >= G->n) { geom_free(G); return -2; }
+  if (run->h_per_knot)
+    for (int r = 0; r < nrows; ++r)
+      if (!(run->h_per_knot[rows[r]] > 0)) { geom_free(G); return -1; }
+  memset(J, 0, sizeof(*J));
+  J->S.G = G; J->S.cf = cf; J->S.dt = run->dt; J->S.h_per_knot = run->h_per_knot;
+  J->S.key[0] = (uint32_t)run->seed; J->S.key[1] = (uint32_t)(run->seed >> 32);
+  J->S.tag = run->tag_word; J->S.k_max = run->k_max;
+  J->scheme = run->scheme;
+  J->n_per_knot = run->n_per_knot; J->n_paths = run->n_paths;
+  J->rows = rows; J->nrows = nrows;
+  return 0;
+}
+
+static int64_t* record_offsets(const job_t* J) {
+  int64_t* off = (int64_t*)malloc((size_t)(J->nrows + 1) * sizeof(int64_t));
+  off[0] = 0;
+  for (int r = 0; r < J->nrows; ++r) off[r + 1] = off[r] + paths_of(J, J->rows[r]);
+  return off;
+}
+
+static void job_run(job_t* J, int32_t threads, int64_t* stats) {
+  pthread_mutex_init(&J->mu, NULL);
+  if (threads < 1) threads = 1;
+  pthread_t* th = (pthread_t*)malloc((size_t)threads * sizeof(pthread_t));
+  for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, worker, J);
+  for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+  free(th);
+  pthread_mutex_destroy(&J->mu);
+  if (stats) for (int i = 0; i < 3; ++i) stats[i] += J->stats[i];
+}
+
+int orc_assemble_ex(const orc_grid* g, const orc_coeffs* cf, const orc_run* run,
+                    const int32_t* rows, int32_t nrows, int32_t threads,
+                    double* val, double* b, orc_record* records, int64_t* stats) {
+  if (run->scheme != ORC_SCHEME_EM && run->scheme != ORC_SCHEME_GM) return -1;
+  geom_t G;
+  job_t J;
+  int rc = job_begin(&J, &G, g, cf, run, rows, nrows);
+  if (rc) return rc;
+  J.row_fn = assemble_row;
+  J.val = val; J.b = b; J.records = records;
+  int64_t* off = records ? record_offsets(&J) : NULL;
+  J.rec_off = off;
+  job_run(&J, threads, stats);
+  free(off);
+  geom_free(&G);
+  return 0;
+}
+
 int orc_assemble(const orc_grid* g, const orc_coeffs* cf,
                  const int64_t* n_per_knot, int64_t n_paths,
                  double dt, uint64_t seed, uint32_t tag_word, int64_t k_max,
                  const int32_t* rows, int32_t nrows, int32_t threads,
                  double* val, double* b, orc_record* records, int64_t* stats) {
-  if (!(dt > 0) || k_max < 1) return -1;
-  geom_t G;
-  if (geom_build(g, &G, 1)) return -1;
-  for (int r = 0; r < nrows; ++r)
-    if (rows[r] < 0 || rows[r] >= G.n) { geom_free(&G); return -2; }
-  job_t J;
-  memset(&J, 0, sizeof(J));
-  J.S.G = &G; J.S.cf = cf; J.S.h = dt; J.S.sqh = sqrt(dt);
-  J.S.key[0] = (uint32_t)seed; J.S.key[1] = (uint32_t)(seed >> 32);
-  J.S.tag = tag_word; J.S.k_max = k_max;
-  J.n_per_knot = n_per_knot; J.n_paths = n_paths;
-  J.rows = rows; J.nrows = nrows; J.val = val; J.b = b; J.records = records;
-  int64_t* off = NULL;
-  if (records) {
-    off = (int64_t*)malloc((size_t)(nrows + 1) * sizeof(int64_t));
-    off[0] = 0;
-    for (int r = 0; r < nrows; ++r) off[r + 1] = off[r] + paths_of(&J, rows[r]);
-    J.rec_off = off;
+  orc_run run;
+  memset(&run, 0, sizeof(run));
+  run.n_per_knot = n_per_knot; run.n_paths = n_paths; run.dt = dt; run.h_per_knot = NULL;
+  run.scheme = ORC_SCHEME_EM; run.tag_word = tag_word; run.seed = seed; run.k_max = k_max;
+  return orc_assemble_ex(g, cf, &run, rows, nrows, threads, val, b, records, stats);
+}
+
+/* ========================================================================= *
+ * Calibration (Sec. 4.1, Phase II): N'_0 mixed GM/EM paths per knot with the  *
+ * warm-up solution u0 as Dirichlet data on the patch boundary.  A score is    *
+ * phi = Y u0(P) + Z, where u0(P) is the stencil interpolation of the nodal    *
+ * u0 on an interface side (the same weights as row k of G) or g on the        *
+ * boundary of Omega; xi (Eq. 37) is kept apart.  Per knot the moments         *
+ *   [N, sum d, sum d^2, sum phi_GM, sum phi_GM^2, sum xi, sum xi^2,           *
+ *    sum phi_GM xi],  d = phi_EM - phi_GM,                                    *
+ * are summed in ascending path order (xi is taken at the GM exit).            *
+ * ========================================================================= */
+static double score_of(const path_out_t* o, const double* u0) {
+  double phi = o->bsum - o->xi;
+  for (int q = 0; q < 2; ++q)
+    if (o->col[q] >= 0) phi += o->w[q] * u0[o->col[q]];
+  return phi;
+}
+
+static void calibrate_row(job_t* J, int r, int64_t* st) {
+  int k = J->rows[r];
+  int64_t N = paths_of(J, k);
+  double m[ORC_CAL_NMOM];
+  for (int i = 0; i < ORC_CAL_NMOM; ++i) m[i] = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    path_out_t em, gm;
+    simulate(&J->S, k, p, 3, &em, &gm);
+    st[0] += em.steps;
+    st[1] += (em.flags & 1) ? 1 : 0;
+    st[2] += ((em.flags | gm.flags) & 2) ? 1 : 0;
+    double pe = score_of(&em, J->u0), pg = score_of(&gm, J->u0), x = gm.xi;
+    double d = pe - pg;
+    m[0] += 1.0;
+    m[1] += d;      m[2] += d * d;
+    m[3] += pg;     m[4] += pg * pg;
+    m[5] += x;      m[6] += x * x;
+    m[7] += pg * x;
+    if (J->cal_records) {
+      orc_cal_record* R = &J->cal_records[J->rec_off[r] + p];
+      R->steps_gm = gm.steps; R->side_gm = gm.side; R->flags_gm = gm.flags;
+      R->steps_em = em.steps; R->side_em = em.side; R->flags_em = em.flags;
+      R->phi_gm = pg; R->phi_em = pe; R->xi_gm = x; R->pad_ = 0.0;
+    }
   }
-  pthread_mutex_init(&J.mu, NULL);
-  if (threads < 1) threads = 1;
-  pthread_t* th = (pthread_t*)malloc((size_t)threads * sizeof(pthread_t));
-  for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, worker, &J);
-  for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
-  free(th);
-  pthread_mutex_destroy(&J.mu);
-  if (stats) for (int i = 0; i < 3; ++i) stats[i] += J.stats[i];
+  for (int i = 0; i < ORC_CAL_NMOM; ++i) J->moments[(size_t)r * ORC_CAL_NMOM + i] = m[i];
+}
+
+int orc_calibrate(const orc_grid* g, const orc_coeffs* cf, const orc_run* run, const double* u0,
+                  const int32_t* rows, int32_t nrows, int32_t threads, double* moments,
+                  orc_cal_record* records, int64_t* stats) {
+  geom_t G;
+  job_t J;
+  int rc = job_begin(&J, &G, g, cf, run, rows, nrows);
+  if (rc) return rc;
+  J.row_fn = calibrate_row;
+  J.u0 = u0; J.moments = moments; J.cal_records = records;
+  int64_t* off = records ? record_offsets(&J) : NULL;
+  J.rec_off = off;
+  job_run(&J, threads, stats);
   free(off);
   geom_free(&G);
   return 0;
+}
+
+/* ========================================================================= *
+ * Setting h_i and N_i from the calibration moments (Sec. 4.2).              *
+ *  gap_i  = mean(phi_EM - phi_GM)            (Eq. 36; the GM bias at h'_0 is   *
+ *                                             bounded by |gap_i| / 2, Eq. 35) *
+ *  V_i    = sample variance of phi_GM,  rho_i^2 = corr(phi_GM, xi)^2 (Eq. 39) *
+ *  h_i    = min(h_0, 2 h'_0 eps / (3 |gap_i|))                       (Eq. 40) *
+ *  N_i    from (2/3) eps = 2 sqrt(V_i (1 - rho_i^2) / N_i), i.e.             *
+ *           N_i = 9 V_i (1 - rho_i^2) / eps^2, rounded to the closest        *
+ *           multiple k N_job with k >= 1                             (Eq. 41) *
+ * diag[3i..3i+2] = gap_i, V_i, rho_i^2 (may be NULL).                        *
+ * ========================================================================= */
+void orc_plan(int64_t n, const double* mom, double eps, double h0, double h0p, int64_t n_job,
+              double* h_out, int64_t* n_out, double* diag) {
+  for (int64_t i = 0; i < n; ++i) {
+    const double* m = mom + (size_t)i * ORC_CAL_NMOM;
+    double N = m[0];
+    double gap = N > 0 ? m[1] / N : 0.0;
+    double var = 0.0, vx = 0.0, cov = 0.0;
+    if (N > 1) {
+      var = (m[4] - m[3] * m[3] / N) / (N - 1.0);
+      vx = (m[6] - m[5] * m[5] / N) / (N - 1.0);
+      cov = (m[7] - m[3] * m[5] / N) / (N - 1.0);
+    }
+    if (var < 0) var = 0;
+    double rho2 = (var > 0 && vx > 0) ? cov * cov / (var * vx) : 0.0;
+    if (rho2 > 1.0) rho2 = 1.0;
+    double h = h0;
+    if (gap != 0.0) {
+      double hb = 2.0 * h0p * eps / (3.0 * fabs(gap));
+      if (hb < h) h = hb;
+    }
+    double nraw = 9.0 * var * (1.0 - rho2) / (eps * eps);
+    double k = nearbyint(nraw / (double)n_job);
+    if (k < 1.0) k = 1.0;
+    h_out[i] = h;
+    n_out[i] = (int64_t)k * n_job;
+    if (diag) { diag[3 * i] = gap; diag[3 * i + 1] = var; diag[3 * i + 2] = rho2; }
+  }
 }
 
 void orc_finalize_rows(const orc_grid* g, const int64_t* row_ptr, const int32_t* col,

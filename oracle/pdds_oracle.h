@@ -22,6 +22,15 @@
  *                                  Lambda^2 scaling, whole-domain patch = plain
  *                                  Feynman-Kac (Eq. 8) on manufactured solutions,
  *                                  drift-only deterministic exit, sqrt(h) bias
+ *   orc_assemble_ex (GM)   pinned: G.1 = b invariant, rectangle exit-time
+ *                                  series (bias O(h) against O(sqrt h) for EM),
+ *                                  harmonic measure of an off-centre point
+ *   orc_calibrate          pinned: EM / GM means equal the rows of the EM / GM
+ *                                  systems applied to u0, constant data give
+ *                                  zero variance, v = 0 gives rho = 0
+ *   orc_plan               pinned: Eq. 40-41 on hand-worked values
+ *   POISSON_E1 coefficients pinned: f against a finite-difference Laplacian
+ *                                  of g = u of Eq. 43
  *   orc_mlp_*              pinned: finite differences, closed-form special cases
  *   orc_lu_solve           pinned: residual and a library dense solve
  *   orc_bicgstab           pinned: agreement with orc_lu_solve and residual
@@ -45,8 +54,18 @@ enum {
                                   u=e^{x/4}cos(y/2), f=Lu, g=u                   */
   ORC_COEF_TABLE          = 3, /* s, c bilinear in FP32 tables, d=0,
                                   f=params[0], g=params[1]                       */
-  ORC_COEF_CONSTANT       = 4  /* s=p0, d=(p1,p2), c=p3, f=p4, g=p5              */
+  ORC_COEF_CONSTANT       = 4, /* s=p0, d=(p1,p2), c=p3, f=p4, g=p5              */
+  ORC_COEF_POISSON_E1     = 5  /* Sec. 5.1: Lap u = f (s=sqrt2, d=0, c=0), u of
+                                  Eq. 43 on [-100,100]^2, f = Lap u, g = u       */
 };
+
+/* Exit schemes (Sec. 2.3). */
+enum {
+  ORC_SCHEME_EM = 0,           /* naive: first step outside the closed patch     */
+  ORC_SCHEME_GM = 1            /* Gobet-Menozzi: sides moved inwards by
+                                  ORC_GM_SHIFT |sigma N| sqrt(h)                  */
+};
+#define ORC_GM_SHIFT 0.5826
 
 typedef struct {
   double x0, x1, y0, y1; /* Omega = [x0,x1] x [y0,y1]                              */
@@ -77,6 +96,29 @@ typedef struct {
   double Y;              /* Y_K = exp(S_K)                                           */
 } orc_record;
 
+/* One path of the mixed GM/EM calibration run (optional output). */
+typedef struct {
+  int32_t steps_gm, side_gm, flags_gm;
+  int32_t steps_em, side_em, flags_em;
+  double phi_gm, phi_em;  /* scores with u0 as patch data (xi excluded)         */
+  double xi_gm;           /* control-variate integral at the GM exit            */
+  double pad_;
+} orc_cal_record;
+#define ORC_CAL_NMOM 8
+
+/* Run parameters of orc_assemble_ex / orc_calibrate. */
+typedef struct {
+  const int64_t* n_per_knot;  /* paths per knot (length n) or NULL: n_paths     */
+  int64_t n_paths;
+  double dt;                  /* reference step                                 */
+  const double* h_per_knot;   /* per-knot step h_k (length n) or NULL: dt        */
+  int64_t k_max;              /* step cap at dt; knot k stops after
+                                 ceil(k_max dt / h_k) steps                     */
+  uint64_t seed;
+  uint32_t tag_word;
+  int32_t scheme;             /* ORC_SCHEME_* (orc_assemble_ex only)            */
+} orc_run;
+
 #define ORC_MLP_HIDDEN 64
 #define ORC_MLP_NPARAM (64 * 2 + 64 + 64 * 64 + 64 + 64 + 1)
 
@@ -103,6 +145,25 @@ int orc_assemble(const orc_grid* g, const orc_coeffs* cf,
                  double dt, uint64_t seed, uint32_t tag_word, int64_t k_max,
                  const int32_t* rows, int32_t nrows, int32_t threads,
                  double* val, double* b, orc_record* records, int64_t* stats);
+
+/* The same with the exit scheme and per-knot steps of `run`. */
+int orc_assemble_ex(const orc_grid* g, const orc_coeffs* cf, const orc_run* run,
+                    const int32_t* rows, int32_t nrows, int32_t threads,
+                    double* val, double* b, orc_record* records, int64_t* stats);
+
+/* Mixed GM/EM calibration run (Sec. 4.1): moments[r][ORC_CAL_NMOM] of
+ * requested row r = [N, sum d, sum d^2, sum phi_GM, sum phi_GM^2, sum xi,
+ * sum xi^2, sum phi_GM xi] with d = phi_EM - phi_GM and u0 (length n) as the
+ * patch data; records (may be NULL) per path as in orc_assemble. */
+int orc_calibrate(const orc_grid* g, const orc_coeffs* cf, const orc_run* run, const double* u0,
+                  const int32_t* rows, int32_t nrows, int32_t threads, double* moments,
+                  orc_cal_record* records, int64_t* stats);
+
+/* Eq. 40-41: per-knot step h_out[i] and path budget n_out[i] from moments
+ * [n][ORC_CAL_NMOM]; diag[3i..3i+2] = mean(phi_EM - phi_GM), var(phi_GM),
+ * rho^2(phi_GM, xi) (diag may be NULL). */
+void orc_plan(int64_t n, const double* moments, double eps, double h0, double h0p,
+              int64_t n_job, double* h_out, int64_t* n_out, double* diag);
 
 /* Finalize: the raw sums in val/b for the given rows become Eq. 24-25 entries. */
 void orc_finalize_rows(const orc_grid* g, const int64_t* row_ptr, const int32_t* col,
