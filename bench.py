@@ -154,6 +154,10 @@ def exact_solution(coef_id: int, xy: np.ndarray):
         return np.sin(np.pi * x) * np.cos(np.pi * y) + x * y
     if coef_id == 2:
         return np.exp(x / 4) * np.cos(y / 2)
+    if coef_id == 5:
+        r = np.sqrt(1 + x * x / 100 + y * y / 50)
+        q = np.sin(3 * x / 25 + y / 20) + np.sin(x / 20 - 3 * y / 25)
+        return 3 + np.sin(r) / 3 + np.tanh(q) / 3
     return None
 
 
@@ -359,7 +363,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "e1"])
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per knot (small profiling cases; not a bench line)")
     ap.add_argument("--no-baseline", action="store_true",
@@ -375,6 +379,8 @@ def main():
         return run_cv_study(args)
     if args.config == "cfg3":
         return run_batch(args)
+    if args.config == "e1":
+        return run_e1(args)
     return run_gpu(args)
 
 
@@ -456,6 +462,66 @@ def run_cv_study(args):
             "config": {"workload": w.name, "knots": res["knots"], "dt": w.dt,
                        "paths_per_knot": n_plain},
             "cv_study": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# The paper's reported E1 figures (Sec. 5.2.1; other hardware and RBF
+# stencils): Phase I and Phase III interfacial errors, the mean variance
+# reduction factor and the mean estimated bias at h0.
+PAPER_E1 = {"phase1": {"max": 0.074, "rmse": 0.016, "frac_below_eps": 0.4898},
+            "phase3": {"max": 0.0224, "rmse": 0.0044, "frac_below_eps": 0.9703},
+            "mean_vrf": 31.37, "mean_bias_at_h0": 3e-5}
+
+
+def run_e1(args):
+    """The paper's experiment (Sec. 5.1) through the calibrated three-phase
+    pipeline (warm-up, mixed GM/EM calibration with Eq. 40-41, production
+    with per-knot N_i, h_i, GM exits and the control variate).  A step is one
+    whole pipeline; the line's value is the path-steps of all three phases
+    over the pipeline's wall time."""
+    import torch
+    from paper_2301_05780_gb300 import calibrated
+    torch.cuda.set_device(0)
+    w = workload("e1")
+    x = w.extra
+    kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"])
+    for _ in range(args.warmup):
+        calibrated.run(w, **kw)
+    runs = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            runs.append(calibrated.run(w, **kw))
+    out = runs[-1]
+    ue = exact_solution(w.coef_id, out["xy"])
+    e1 = calibrated.error_summary(out["phase1"]["u"], ue, x["eps"])
+    e3 = calibrated.error_summary(out["phase3"]["u"], ue, x["eps"])
+    total_ms = [r["phase1"]["ms"] + r.get("fit", {}).get("ms", 0.0) + r["phase2"]["ms"] +
+                r["phase3"]["ms"] for r in runs]
+    steps = [r["phase1"]["path_steps"] + 2 * r["phase2"]["path_steps_gm_pass"] +
+             r["phase3"]["path_steps"] for r in runs]
+    p2 = out["phase2"]
+    line = {"metric": METRIC, "value": float(np.sum(steps) / (np.sum(total_ms) * 1e-3)),
+            "unit": "path-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(total_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "knots": out["knots"], "eps": x["eps"],
+                       "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
+                       "note": "path-steps of the GM pass counted twice for the mixed run"},
+            "pipeline": {
+                "phase1": {"ms": out["phase1"]["ms"], "path_steps": out["phase1"]["path_steps"],
+                           "errors": e1},
+                "fit_ms": out.get("fit", {}).get("ms"),
+                "phase2": {"ms": p2["ms"], "mean_bias_bound": p2["mean_bias_bound"],
+                           "mean_predicted_vrf": p2["mean_predicted_vrf"],
+                           "knots_with_h_below_h0": p2["knots_with_h_below_h0"],
+                           "N_mean": float(np.mean(p2["N"])), "N_max": int(np.max(p2["N"])),
+                           "h_min": float(np.min(p2["h"]))},
+                "phase3": {"ms": out["phase3"]["ms"], "path_steps": out["phase3"]["path_steps"],
+                           "paths": out["phase3"]["paths"], "errors": e3,
+                           "truncated": out["phase3"]["truncated"]},
+                "paper": PAPER_E1},
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
 

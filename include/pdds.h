@@ -71,7 +71,11 @@ enum {
                                    f = L u for u = e^{x/4} cos(y/2), g = u              */
   PDDS_COEF_TABLE = 3,          /* s and c bilinear in FP32 tables, d = 0,
                                    f = params[0], g = params[1] (constants)           */
-  PDDS_COEF_CONSTANT = 4        /* s = p0, d = (p1, p2), c = p3, f = p4, g = p5        */
+  PDDS_COEF_CONSTANT = 4,       /* s = p0, d = (p1, p2), c = p3, f = p4, g = p5        */
+  PDDS_COEF_POISSON_E1 = 5      /* Sec. 5.1, Eq. 42-43: Lap u = f on [-100,100]^2, i.e.
+                                   s = sqrt2, d = 0, c = 0, f = Lap u and g = u for
+                                   u = 3 + sin(r)/3 + tanh(q)/3, r = sqrt(1 + x^2/100
+                                   + y^2/50), q = sin(3x/25 + y/20) + sin(x/20 - 3y/25) */
 };
 enum { PDDS_COEF_BUILTIN = 0 };
 
@@ -92,7 +96,7 @@ typedef struct {
   double* val;
 } pdds_csr;
 
-/* Per-path record written by pdds_assemble_records (32 bytes). */
+/* Per-path record written by pdds_assemble_records (40 bytes). */
 typedef struct {
   int32_t steps;      /* K, Euler-Maruyama steps taken                                */
   int32_t side_flags; /* exit side (0 E, 1 N, 2 W, 3 S) | flags << 8: bit0 step cap,
@@ -101,6 +105,8 @@ typedef struct {
   float w_a, w_b;     /* Y_K times the interpolation weight                           */
   float b_contrib;    /* Z_K + xi_K + boundary terms: the path's share of b_k times N */
   float Y;            /* Y_K = exp(int c dt)                                          */
+  float xi;           /* xi_K alone (0 without a control variate)                     */
+  int32_t pad_;
 } pdds_path_record;
 
 typedef struct {
@@ -194,6 +200,57 @@ pdds_status pdds_assemble_records(pdds_ctx* ctx, const int64_t* n_per_knot, int6
                                   double dt, uint64_t seed, pdds_csr* G, double* b,
                                   pdds_path_record* records, void* cuda_stream);
 
+/* Exit scheme of the path kernel (Sec. 2.3):
+ *  PDDS_SCHEME_EM  naive Euler-Maruyama: exit at the first step outside the
+ *                  closed patch (weak order 1/2; the default);
+ *  PDDS_SCHEME_GM  Gobet-Menozzi: every patch side is moved inwards by
+ *                  0.5826 |s(P)| sqrt(h), P the normal projection of the
+ *                  current point on that side, and the path exits at the first
+ *                  step beyond a moved side (weak order 1).  The exit side is the
+ *                  one of smallest positive overshoot past its moved line; the
+ *                  exit point is the normal projection on the true side.
+ * Applies to every later assemble / calibrate call on ctx (not to batches). */
+enum { PDDS_SCHEME_EM = 0, PDDS_SCHEME_GM = 1 };
+pdds_status pdds_set_scheme(pdds_ctx* ctx, int32_t scheme);
+
+/* Per-knot time steps h_k (Sec. 4.2, Eq. 40).  h_per_knot: DEVICE double[n],
+ * every h_k > 0 and finite, copied into the context (synchronizes; the caller
+ * may free it afterwards); NULL returns to the single dt of each call.  While
+ * set, knot k steps with h_k and the dt argument of assemble / calibrate only
+ * fixes the time horizon of the step cap: knot k stops after
+ * ceil(k_max dt / h_k) steps.  Not used by pdds_assemble_batch. */
+pdds_status pdds_set_knot_steps(pdds_ctx* ctx, const double* h_per_knot);
+
+/* Calibration run of Sec. 4.1 (Phase II): N_k "mixed GM/EM" paths per knot
+ * with the warm-up nodal solution u0 as the data on the patch boundary.  Every
+ * path yields a Gobet-Menozzi score phi_GM (first step beyond a moved side)
+ * and a naive score phi_EM (first step outside the patch) from one trajectory
+ * (the same Philox counters as pdds_assemble with `seed`), where
+ * phi = Y u0(P) + Z, u0(P) being the stencil interpolation of the nodal u0 on
+ * an interface side and g on the boundary of Omega; with a control variate
+ * attached, xi (Eq. 37, up to the GM exit) is drawn alongside.  Per knot:
+ *   moments[k][0..7] = N_k, sum d, sum d^2, sum phi_GM, sum phi_GM^2,
+ *                      sum xi, sum xi^2, sum phi_GM xi      (d = phi_EM - phi_GM)
+ * in FP64 (DEVICE double[n][8]).  u0: DEVICE double[n]; n_per_knot / n_paths /
+ * dt / seed as for pdds_assemble (per-knot steps apply when set).  The scheme
+ * setting is ignored.  Allocates context-owned record scratch (40 bytes per
+ * path and pass, kept for reuse) and synchronizes the stream. */
+pdds_status pdds_calibrate(pdds_ctx* ctx, const double* u0, const int64_t* n_per_knot,
+                           int64_t n_paths, double dt, uint64_t seed, double* moments,
+                           void* cuda_stream);
+
+/* Eq. 40-41: per-knot steps and path budgets for accuracy eps from the
+ * calibration moments (DEVICE double[n][8], as written by pdds_calibrate):
+ *   gap_k = mean d,  V_k = sample variance of phi_GM,  rho_k^2 = corr(phi_GM, xi)^2
+ *   h_out[k] = min(h0, 2 h0' eps / (3 |gap_k|))        (h0 when gap_k = 0)
+ *   N_out[k] = N_job * max(1, round(9 V_k (1 - rho_k^2) / (eps^2 N_job)))
+ * (rounding half to even).  h_out: DEVICE double[n]; N_out: DEVICE int64[n];
+ * diag (nullable): DEVICE double[n][3] = gap_k, V_k, rho_k^2.  No context;
+ * asynchronous.  EINVAL for n < 1, eps, h0 or h0' not > 0, or N_job < 1. */
+pdds_status pdds_plan(const double* moments, int64_t n, double eps, double h0, double h0p,
+                      int64_t n_job, double* h_out, int64_t* n_out, double* diag,
+                      void* cuda_stream);
+
 /* Several independent problems (same coefficient set id) in ONE persistent
  * launch: paths of all problems share one work queue.  Arrays have `count`
  * entries; n_per_knot[i] may be NULL (then n_paths is used).  Problem i uses
@@ -245,7 +302,8 @@ pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, flo
  * on pdds_assemble adds xi_K = -sum_n Y_n s(X_n) grad v(X_n) . dW_n to every
  * path's b contribution (Eq. 37, left-point Ito sum), which leaves E[b]
  * unchanged and lowers its variance as v approaches u.  NULL detaches it.
- * Available for PDDS_COEF_LAPLACE_EXPSIN, _MANUFACTURED and _CONSTANT. */
+ * Available for PDDS_COEF_LAPLACE_EXPSIN, _MANUFACTURED, _CONSTANT and
+ * _POISSON_E1. */
 pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
 
 /* Allocation-free variant of pdds_solve (the paper has no counterpart; this

@@ -243,6 +243,15 @@ struct pdds_ctx {
   void* d_mlp = nullptr;
   bool cv_on = false;
   bool unit_domain_all = false;  // set by a batched launch: all its domains in [-1,1]^2
+  // exit scheme and per-knot steps (extended-exit kernels)
+  int scheme = PDDS_SCHEME_EM;
+  double* d_hknot = nullptr;  // owned copy of h_k, or nullptr
+  double h_min = 0;           // smallest h_k (wait bound)
+  // calibration scratch: records of the naive and the GM pass, a CSR and b
+  pdds_path_record* cal_rec = nullptr;
+  int64_t cal_rec_cap = 0;    // records per pass
+  double *cal_val = nullptr, *cal_b = nullptr;
+  int32_t *cal_rp = nullptr, *cal_col = nullptr;
   std::vector<uint64_t> graph_key;
   pdds_stats_t st{};
   std::string err = "no error";
@@ -278,6 +287,8 @@ void free_ctx(pdds_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_mlp);
+  cudaFree(c->d_hknot); cudaFree(c->cal_rec); cudaFree(c->cal_val); cudaFree(c->cal_b);
+  cudaFree(c->cal_rp); cudaFree(c->cal_col);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -323,6 +334,8 @@ ProbDesc make_prob(const pdds_ctx* c, int tag) {
     D.tab_ny = c->tab_ny;
   }
   D.tag = tag;
+  D.sigma_max = (float)(c->s_max * (1.0 + 1e-6));  // bilinear lookups may round up 1 ulp
+  D.h_per_knot = c->d_hknot;
   D.knots = c->d_knots;
   D.slot2csr = c->d_slot2csr;
   D.col = c->d_col;
@@ -345,10 +358,11 @@ int64_t default_kmax(const pdds_ctx* c, double dt) {
 }
 
 // Everything one or more problems need for one persistent launch.
+// ext: extended-exit kernel (per-knot steps and/or the Gobet-Menozzi shift gm).
 pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, int nprob,
                       double dt, uint64_t seed, int64_t kmax, pdds::PathRecordDev* rec,
                       cudaStream_t stream, size_t sbytes, int max_slots, int tile_w, int tile_h,
-                      int coef_id) {
+                      int coef_id, bool ext = false, bool gm = false) {
   pdds::KParams kp{};
   kp.prob0 = p0;
   kp.probs = d_probs;
@@ -363,13 +377,18 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   kp.h = (float)dt;
   kp.sqh = (float)std::sqrt(dt);
   kp.kmax = kmax;
+  kp.dt = dt;
+  kp.gm = gm ? 1 : 0;
   kp.max_slots = max_slots;
   kp.tile_w = tile_w;
   kp.tile_h = tile_h;
   kp.stage_bytes = (int)sbytes;
   kp.rec_mode = rec != nullptr;
   // a wait may outlast the slowest path of a unit: K_max steps at ~4 us
-  kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * (double)kmax);
+  // (per-knot steps: the longest cap is kmax dt / h_min steps)
+  const double kmax_eff = ext && c->d_hknot && c->h_min < dt ? (double)kmax * dt / c->h_min
+                                                             : (double)kmax;
+  kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * kmax_eff);
   const bool cv = nprob == 1 && c->cv_on;
   kp.mlp = cv ? c->d_mlp : nullptr;
   {
@@ -381,25 +400,27 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
     kp.unit_domain = (nprob == 1 ? u0 : c->unit_domain_all) ? 1 : 0;
   }
   // the control-variate step is ~10x heavier: wait bounds scale with it
-  if (cv && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * (double)kmax);
+  if (cv && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
   // CV kernels keep the staged network at the start of dynamic shared memory
   const size_t smem = 2 * sbytes + (cv ? round_up(pdds::mlp_image_bytes(), 128) : 0);
-  CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, smem));
+  CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, ext, smem));
   const int block = cv ? std::min(c->block, 256) : c->block;  // CV kernels: <= 256 threads
   int per_sm = c->ctas_per_sm;
   if (per_sm <= 0) {
-    CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, block, smem, &per_sm));
+    CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, ext, block, smem, &per_sm));
     if (per_sm <= 0) return fail(c, PDDS_EINVAL, "launch: block/shared memory too large");
   }
   const int grid = c->num_sms * per_sm;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
-  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, kp, grid, block, smem, stream));
+  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, ext, kp, grid, block, smem, stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
   return PDDS_OK;
 }
 
+// scheme: PDDS_SCHEME_EM / _GM, or -1 for the context's setting.
 pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, uint64_t seed,
-                          pdds_csr* G, double* b, pdds_path_record* rec, cudaStream_t s) {
+                          pdds_csr* G, double* b, pdds_path_record* rec, cudaStream_t s,
+                          int scheme = -1) {
   (void)cudaGetLastError();  // a failed call elsewhere must not be reported here
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PDDS_EINVAL, "assemble: dt must be > 0");
   if (!N && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
@@ -429,9 +450,11 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   }
   CK(c, pdds::launch_prob_prefix_single(D, c->d_prob_prefix, s));
   ++launches;
+  const bool gm = (scheme < 0 ? c->scheme : scheme) == PDDS_SCHEME_GM;
+  const bool ext = gm || c->d_hknot != nullptr;
   if (pdds_status e = run_paths(c, D, nullptr, 1, dt, seed, kmax,
                                 reinterpret_cast<pdds::PathRecordDev*>(rec), s, stage_bytes(c),
-                                c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id))
+                                c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id, ext, gm))
     return e;
   ++launches;
   CK(c, pdds::launch_finalize(G->row_ptr, G->col, G->val, b, N, Nu, c->geo.n, s));
@@ -474,7 +497,7 @@ pdds_status pdds_geometry_host(const pdds_grid* grid, int64_t* n, int64_t* nnz, 
 pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx** out) {
   if (!grid || !cf || !out) return fail(nullptr, PDDS_EINVAL, "create: NULL argument");
   *out = nullptr;
-  if (cf->kind != PDDS_COEF_BUILTIN || cf->builtin_id < 0 || cf->builtin_id > PDDS_COEF_CONSTANT)
+  if (cf->kind != PDDS_COEF_BUILTIN || cf->builtin_id < 0 || cf->builtin_id > PDDS_COEF_POISSON_E1)
     return fail(nullptr, PDDS_EINVAL, "create: unknown coefficient set");
   auto* c = new (std::nothrow) pdds_ctx;
   if (!c) return fail(nullptr, PDDS_ENOMEM, "create: out of host memory");
@@ -681,17 +704,19 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   if (n_paths < 1 || !(dt > 0)) return fail(c, PDDS_EINVAL, "autotune: need n_paths >= 1, dt > 0");
   // Cache key: device, coefficient set, control variate, grid shape, budget.
   struct Key {
-    int dev, coef, cv, Hx, Hy, m, ext;
+    int dev, coef, cv, xk, Hx, Hy, m, ext;
     int64_t N;
     bool operator<(const Key& o) const {
-      return std::tie(dev, coef, cv, Hx, Hy, m, ext, N) <
-             std::tie(o.dev, o.coef, o.cv, o.Hx, o.Hy, o.m, o.ext, o.N);
+      return std::tie(dev, coef, cv, xk, Hx, Hy, m, ext, N) <
+             std::tie(o.dev, o.coef, o.cv, o.xk, o.Hx, o.Hy, o.m, o.ext, o.N);
     }
   };
   struct Shape { int block, unit, batch; };
   static std::mutex mu;
   static std::map<Key, Shape> cache;
-  const Key key{c->device, c->coef_id, c->cv_on ? 1 : 0, c->grid.Hx, c->grid.Hy, c->grid.m,
+  // xk: the extended-exit kernel (GM scheme or per-knot steps) is a different kernel
+  const int xk = (c->scheme == PDDS_SCHEME_GM ? 1 : 0) + (c->d_hknot ? 2 : 0);
+  const Key key{c->device, c->coef_id, c->cv_on ? 1 : 0, xk, c->grid.Hx, c->grid.Hy, c->grid.m,
                 c->grid.ext, n_paths};
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -775,6 +800,109 @@ pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
 pdds_status pdds_set_timing(pdds_ctx* c, int32_t on) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_timing: NULL context");
   c->timing = on != 0;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_scheme(pdds_ctx* c, int32_t scheme) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_scheme: NULL context");
+  if (scheme != PDDS_SCHEME_EM && scheme != PDDS_SCHEME_GM)
+    return fail(c, PDDS_EINVAL, "set_scheme: scheme must be PDDS_SCHEME_EM or PDDS_SCHEME_GM");
+  c->scheme = scheme;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_knot_steps(pdds_ctx* c, const double* h) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_knot_steps: NULL context");
+  (void)cudaGetLastError();
+  if (!h) {
+    CK(c, cudaFree(c->d_hknot));
+    c->d_hknot = nullptr;
+    c->h_min = 0;
+    return PDDS_OK;
+  }
+  const int64_t n = c->geo.n;
+  std::vector<double> hh(n);
+  CK(c, cudaMemcpy(hh.data(), h, n * 8, cudaMemcpyDefault));
+  double lo = 1e300;
+  for (double v : hh) {
+    if (!(v > 0) || !std::isfinite(v))
+      return fail(c, PDDS_EINVAL, "set_knot_steps: every h_k must be finite and > 0");
+    lo = std::min(lo, v);
+  }
+  if (!c->d_hknot) CK(c, dalloc(&c->d_hknot, n));
+  CK(c, cudaMemcpy(c->d_hknot, hh.data(), n * 8, cudaMemcpyHostToDevice));
+  c->h_min = lo;
+  return PDDS_OK;
+}
+
+pdds_status pdds_calibrate(pdds_ctx* c, const double* u0, const int64_t* N, int64_t Nu, double dt,
+                           uint64_t seed, double* moments, void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "calibrate: NULL context");
+  if (!u0 || !moments) return fail(c, PDDS_EINVAL, "calibrate: u0 and moments are required");
+  (void)cudaGetLastError();
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = c->geo.n, nnz = c->geo.nnz;
+  // records per pass: sum of N_k
+  int64_t total = 0;
+  if (N) {
+    std::vector<int64_t> Nh(n);
+    CK(c, cudaMemcpyAsync(Nh.data(), N, n * 8, cudaMemcpyDefault, s));
+    CK(c, cudaStreamSynchronize(s));
+    for (int64_t v : Nh) {
+      if (v < 0 || v >= ((int64_t)1 << 31))
+        return fail(c, PDDS_EINVAL, "calibrate: every N_k must be in [0, 2^31)");
+      total += v;
+    }
+  } else {
+    if (Nu < 1 || Nu >= ((int64_t)1 << 31))
+      return fail(c, PDDS_EINVAL, "calibrate: n_paths must be in [1, 2^31)");
+    total = Nu * n;
+  }
+  if (total > c->cal_rec_cap) {
+    CK(c, cudaFree(c->cal_rec));
+    c->cal_rec = nullptr;
+    c->cal_rec_cap = 0;
+    if (dalloc(&c->cal_rec, 2 * (size_t)std::max<int64_t>(total, 1)) != cudaSuccess)
+      return fail(c, PDDS_ENOMEM, "calibrate: record scratch allocation failed");
+    c->cal_rec_cap = total;
+  }
+  if (!c->cal_val) {
+    if (dalloc(&c->cal_val, nnz) || dalloc(&c->cal_b, n) || dalloc(&c->cal_rp, n + 1) ||
+        dalloc(&c->cal_col, nnz))
+      return fail(c, PDDS_ENOMEM, "calibrate: CSR scratch allocation failed");
+  }
+  pdds_csr G{n, nnz, c->cal_rp, c->cal_col, c->cal_val};
+  pdds_path_record* rec_em = c->cal_rec;
+  pdds_path_record* rec_gm = c->cal_rec + c->cal_rec_cap;
+  // the same counters in both passes, so both passes follow the same paths: the
+  // GM pass stops at the first step beyond a moved side, the naive pass goes
+  // on to the first step outside the patch -- the mixed trajectory of Sec. 4.1
+  if (pdds_status e = assemble_impl(c, N, Nu, dt, seed, &G, c->cal_b, rec_em, s, PDDS_SCHEME_EM))
+    return e;
+  const int launches = c->st.kernel_launches;
+  const pdds_stats_t em_st = c->st;
+  if (pdds_status e = assemble_impl(c, N, Nu, dt, seed, &G, c->cal_b, rec_gm, s, PDDS_SCHEME_GM))
+    return e;
+  CK(c, pdds::launch_calib_moments(reinterpret_cast<const pdds::PathRecordDev*>(rec_em),
+                                   reinterpret_cast<const pdds::PathRecordDev*>(rec_gm),
+                                   N ? c->d_path_prefix : nullptr, Nu, u0, n, moments, s));
+  CK(c, cudaStreamSynchronize(s));
+  c->st.kernel_launches += launches + 1;
+  c->st.path_kernel_ms += em_st.path_kernel_ms;
+  return PDDS_OK;
+}
+
+pdds_status pdds_plan(const double* moments, int64_t n, double eps, double h0, double h0p,
+                      int64_t n_job, double* h_out, int64_t* n_out, double* diag, void* stream) {
+  (void)cudaGetLastError();
+  if (!moments || !h_out || !n_out)
+    return fail(nullptr, PDDS_EINVAL, "plan: moments, h_out and n_out are required");
+  if (n < 1 || !(eps > 0) || !(h0 > 0) || !(h0p > 0) || n_job < 1 || !std::isfinite(eps) ||
+      !std::isfinite(h0) || !std::isfinite(h0p))
+    return fail(nullptr, PDDS_EINVAL, "plan: need n >= 1, eps, h0, h0' > 0 and N_job >= 1");
+  cudaError_t e = pdds::launch_plan(moments, n, eps, h0, h0p, n_job, h_out, n_out, diag,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, PDDS_ECUDA, std::string("plan: ") + cudaGetErrorString(e));
   return PDDS_OK;
 }
 
@@ -902,6 +1030,10 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same device");
     if (c->cv_on)
       return fail(c0, PDDS_EINVAL, "assemble_batch: control variates are not supported in batches");
+    if (c->scheme != PDDS_SCHEME_EM || c->d_hknot)
+      return fail(c0, PDDS_EINVAL,
+                  "assemble_batch: the Gobet-Menozzi scheme and per-knot steps are not supported "
+                  "in batches");
     if (pdds_status e = check_csr(c, G[i], b[i])) return fail(c0, e, c->err);
     if (!(N && N[i]) && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
       return fail(c0, PDDS_EINVAL, "assemble_batch: n_paths must be in [1, 2^31)");
@@ -961,7 +1093,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       if (c0->coef_id == PDDS_COEF_TABLE) x += 2 * round_up((size_t)tw * th * 4, 128);
       return round_up(x, 128);
     }();
-    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, false, 2 * sb));
+    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, false, false, 2 * sb));
     // Capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the instantiated graph is launched on the caller's.
     if (!c0->cap_stream) CK(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));

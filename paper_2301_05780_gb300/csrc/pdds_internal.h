@@ -56,6 +56,9 @@ struct ProbDesc {
   const CUtensorMap* tmap;        // TABLE: [2] = sigma, c (device global memory)
   int32_t tab_nx, tab_ny;        // TABLE: table nodes
   const int32_t* col;             // CSR column of each value (records mode)
+  const double* h_per_knot;       // per-knot steps (extended-exit kernels), or nullptr
+  float sigma_max;                // upper bound of s(x) over the closure of Omega
+  int32_t pad1_;
 };
 
 // Device-side counters of one launch (zeroed before each assemble).
@@ -72,8 +75,10 @@ struct Scratch {
 
 struct PathRecordDev {
   int32_t steps, side_flags, col_a, col_b;
-  float w_a, w_b, b_contrib, Y;
+  float w_a, w_b, b_contrib, Y, xi;
+  int32_t pad_;
 };
+static_assert(sizeof(PathRecordDev) == 40, "record layout of pdds_path_record");
 
 struct KParams {
   ProbDesc prob0;                   // the problem when nprob == 1
@@ -96,15 +101,17 @@ struct KParams {
   uint64_t wait_ns;        // bound on any device-side wait
   const void* mlp;         // staged control-variate network (MlpSmem), or nullptr
   int32_t unit_domain;     // every problem's Omega lies in [-1, 1]^2 (no trig reduction)
-  int32_t pad2_;
+  int32_t gm;              // extended kernels: 1 = Gobet-Menozzi shift of the sides
+  double dt;               // extended kernels: step at which kmax counts
 };
 
 // Launchers implemented in the .cu files (host-callable).
-cudaError_t launch_path_kernel(int coef_id, bool records, bool cv, const KParams& kp, int grid,
-                               int block, size_t smem, cudaStream_t stream);
-cudaError_t path_kernel_occupancy(int coef_id, bool records, bool cv, int block, size_t smem,
-                                  int* ctas_per_sm);
-cudaError_t set_path_kernel_smem(int coef_id, bool records, bool cv, size_t smem);
+// `ext` selects the extended-exit variants (per-knot steps, Gobet-Menozzi shift).
+cudaError_t launch_path_kernel(int coef_id, bool records, bool cv, bool ext, const KParams& kp,
+                               int grid, int block, size_t smem, cudaStream_t stream);
+cudaError_t path_kernel_occupancy(int coef_id, bool records, bool cv, bool ext, int block,
+                                  size_t smem, int* ctas_per_sm);
+cudaError_t set_path_kernel_smem(int coef_id, bool records, bool cv, bool ext, size_t smem);
 bool path_kernel_has_cv(int coef_id);
 // Control-variate network (pdds_mlp.cu): FP32 theta -> staged image.
 size_t mlp_image_bytes();
@@ -118,6 +125,15 @@ size_t stage_header_bytes();
 cudaError_t launch_finalize(const int32_t* row_ptr, const int32_t* col, double* val, double* b,
                             const int64_t* n_per_knot, int64_t n_paths, int64_t n,
                             cudaStream_t stream);
+
+// Calibration (pdds_calib.cu): per-knot moments of the mixed GM/EM scores
+// from the records of the naive and the Gobet-Menozzi pass, and Eq. 40-41.
+cudaError_t launch_calib_moments(const PathRecordDev* rec_em, const PathRecordDev* rec_gm,
+                                 const int64_t* path_prefix, int64_t n_paths, const double* u0,
+                                 int64_t n, double* moments, cudaStream_t stream);
+cudaError_t launch_plan(const double* moments, int64_t n, double eps, double h0, double h0p,
+                        int64_t n_job, double* h_out, int64_t* n_out, double* diag,
+                        cudaStream_t stream);
 
 // FP64 BiCGSTAB building blocks (pdds_solve.cu).
 struct SolveScalars;

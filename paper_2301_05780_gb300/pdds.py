@@ -57,7 +57,11 @@ class pdds_stats_t(C.Structure):
 
 RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side_flags", "<i4"), ("col_a", "<i4"),
                          ("col_b", "<i4"), ("w_a", "<f4"), ("w_b", "<f4"), ("b_contrib", "<f4"),
-                         ("Y", "<f4")])
+                         ("Y", "<f4"), ("xi", "<f4"), ("pad_", "<i4")])
+RECORD_BYTES = RECORD_DTYPE.itemsize  # 40, as pdds_path_record
+
+PDDS_SCHEME_EM, PDDS_SCHEME_GM = 0, 1
+CAL_NMOM = 8
 
 # name -> (restype, argtypes); mirrors include/pdds.h
 _P = C.c_void_p
@@ -76,6 +80,11 @@ _SIGS = {
     "pdds_assemble": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P]),
     "pdds_assemble_records": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P,
                                         _P]),
+    "pdds_set_scheme": (C.c_int, [_P, C.c_int32]),
+    "pdds_set_knot_steps": (C.c_int, [_P, _P]),
+    "pdds_calibrate": (C.c_int, [_P, _P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P]),
+    "pdds_plan": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64, _P, _P,
+                            _P, _P]),
     "pdds_assemble_batch": (C.c_int, [_P, C.c_int32, _P, C.c_int64, C.c_double, C.c_uint64, _P,
                                       _P, _P]),
     "pdds_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, _P, _P]),
@@ -214,6 +223,10 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _dptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
 def _csr_struct(G):
     rp, col, val = G
     return pdds_csr(rp.numel() - 1, col.numel(), rp.data_ptr(), col.data_ptr(), val.data_ptr())
@@ -229,13 +242,39 @@ def pdds_assemble(ctx, G, b, n_paths=0, n_per_knot=None, dt=1e-4, seed=0, stream
 
 def pdds_assemble_records(ctx, G, b, records, n_paths=0, n_per_knot=None, dt=1e-4, seed=0,
                           stream=None):
-    """records: device uint8 tensor of sum_k N_k * 32 bytes."""
+    """records: device uint8 tensor of sum_k N_k * RECORD_BYTES bytes."""
     csr = _csr_struct(G)
     Np = None if n_per_knot is None else C.c_void_p(n_per_knot.data_ptr())
     _check(lib().pdds_assemble_records(ctx, Np, int(n_paths), float(dt),
                                        C.c_uint64(int(seed) % 2**64), C.byref(csr),
                                        C.c_void_p(b.data_ptr()), C.c_void_p(records.data_ptr()),
                                        _stream(stream)), ctx)
+
+
+def pdds_set_scheme(ctx, scheme: int):
+    """PDDS_SCHEME_EM (naive exit) or PDDS_SCHEME_GM (Gobet-Menozzi shift)."""
+    _check(lib().pdds_set_scheme(ctx, int(scheme)), ctx)
+
+
+def pdds_set_knot_steps(ctx, h_per_knot):
+    """Per-knot steps (device float64 tensor [n], copied) or None."""
+    _check(lib().pdds_set_knot_steps(ctx, _dptr(h_per_knot)), ctx)
+
+
+def pdds_calibrate(ctx, u0, moments, n_paths=0, n_per_knot=None, dt=1e-4, seed=0, stream=None):
+    """Mixed GM/EM calibration run: moments (device float64 [n, 8]) from the
+    warm-up nodal solution u0 (device float64 [n])."""
+    _check(lib().pdds_calibrate(ctx, _dptr(u0), _dptr(n_per_knot), int(n_paths), float(dt),
+                                C.c_uint64(int(seed) % 2**64), _dptr(moments), _stream(stream)),
+           ctx)
+
+
+def pdds_plan(moments, eps, h0, h0p, n_job, h_out, n_out, diag=None, stream=None):
+    """Eq. 40-41 on device tensors: h_out float64 [n], n_out int64 [n],
+    diag (optional) float64 [n, 3] = (gap, var, rho^2)."""
+    n = h_out.numel()
+    _check(lib().pdds_plan(_dptr(moments), n, float(eps), float(h0), float(h0p), int(n_job),
+                           _dptr(h_out), _dptr(n_out), _dptr(diag), _stream(stream)))
 
 
 def pdds_assemble_batch(ctxs, Gs, bs, n_paths=0, n_per_knot=None, dt=1e-5, seed=0, stream=None):
@@ -278,10 +317,6 @@ def pdds_solve_noalloc(G, b, u, rtol=1e-12, maxit=2000, stream=None, n=None):
 
 
 MLP_NPARAM = 4417
-
-
-def _dptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
 
 
 def pdds_mlp_loss_grad(theta, xy, target, stream=None):
@@ -387,7 +422,7 @@ class Problem:
 
     def records_buffer(self):
         import torch
-        return torch.empty(self.total_paths() * 32, dtype=torch.uint8, device=self.dev)
+        return torch.empty(self.total_paths() * RECORD_BYTES, dtype=torch.uint8, device=self.dev)
 
     def close(self):
         if self.ctx:

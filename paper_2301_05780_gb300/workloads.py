@@ -6,11 +6,11 @@ coefficient tables.  It holds none of the method's arithmetic, so both the
 CUDA library (through ``bench.py``) and the FP64 oracle (through the tests)
 can be fed from it.
 
-The five workloads mirror the shapes of the paper's experiments (Sec. 5,
+The five configurations mirror the shapes of the paper's experiments (Sec. 5,
 Table 1): 2-D square domains cut into H x H subdomains, interfacial knots at
 spacing 1/(H m), Euler-Maruyama paths confined to patches.  The paper's own
-experiment (Poisson on [-100,100]^2 with the closed-form solution of Eq. 43)
-needs no dataset; these synthetic problems stand in for it.
+experiment (Sec. 5.1: Poisson on [-100,100]^2 with the closed-form solution of
+Eq. 43) needs no dataset; ``paper_e1`` sets it up with the paper's sizes.
 """
 from __future__ import annotations
 
@@ -26,6 +26,7 @@ COEF_MANUFACTURED = 1     # sigma=sqrt2, d=(sin 2pi y, cos 2pi x), c=-(1+x^2), u
 COEF_VARSIGMA = 2         # sigma=sqrt2(1+0.3 sin 2pi x sin 2pi y), d=0, c=-1, u=e^{x/4}cos(y/2)
 COEF_TABLE = 3            # sigma, c from FP32 tables; d=0; f=params[0]; g=params[1]
 COEF_CONSTANT = 4         # sigma=p0, d=(p1,p2), c=p3, f=p4, g=p5
+COEF_POISSON_E1 = 5       # Sec. 5.1: sigma=sqrt2, d=0, c=0, f=Lap u, g=u of Eq. 43
 
 SEED_BASE = 2301057800
 
@@ -178,6 +179,19 @@ def config5() -> Workload:
                             n_paths=100_000, dt=1e-6, seed=SEED_BASE + 5))
 
 
+def paper_e1() -> Workload:
+    """The paper's experiment (Sec. 5.1): Lap u = f on [-100,100]^2 with u of
+    Eq. 43, 10x10 subdomains, 64 knots per interface segment (m = 63
+    intervals): 11,241 unknown knots (11,277 with the 36 boundary line ends
+    the paper keeps as trivial rows).  Warm-up and calibration use
+    N0 = N0' = 1000 paths and h0 = h0' = 0.08; the production run aims at
+    eps = 0.01 with budgets in multiples of N_job = 200."""
+    w = Workload("paper_e1_poisson_10x10", _grid(-100, 100, -100, 100, 10, 63), COEF_POISSON_E1,
+                 n_paths=1000, dt=0.08, seed=SEED_BASE + 6,
+                 extra=dict(eps=0.01, n_job=200, n0=1000, h0=0.08))
+    return _finish(w)
+
+
 def mlp_init(seed: int = SEED_BASE + 55) -> np.ndarray:
     """Seeded initial parameters of v_theta (2 -> 64 -> 64 -> 1), layout
     W1[64][2], b1[64], W2[64][64], b2[64], w3[64], b3 (fan-in scaled normals)."""
@@ -192,4 +206,5 @@ def mlp_init(seed: int = SEED_BASE + 55) -> np.ndarray:
 
 
 def all_configs() -> dict:
-    return {"cfg1": config1, "cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5}
+    return {"cfg1": config1, "cfg2": config2, "cfg3": config3, "cfg4": config4, "cfg5": config5,
+            "e1": paper_e1}

@@ -67,3 +67,23 @@ def test_host_geometry_rejects_invalid_grids(bad):
         pdds.pdds_geometry_host(bad)
     assert e.value.status == pdds.PDDS_EINVAL
     assert "grid" in str(e.value)
+
+
+def test_record_and_struct_layouts_match_the_header(tmp_path):
+    """The binding's record dtype and structs have the sizes the C header gives
+    (compiled with the host C compiler, no CUDA)."""
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "pdds.h"\nint main(void){printf("%zu %zu %zu %zu",'
+                   ' sizeof(pdds_path_record), sizeof(pdds_grid), sizeof(pdds_coeffs),'
+                   ' sizeof(pdds_stats_t)); return 0;}\n')
+    exe = tmp_path / "sz"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    rec, grid, coeffs, stats = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.split())
+    import ctypes
+    assert rec == pdds.RECORD_BYTES == 40
+    assert grid == ctypes.sizeof(pdds.pdds_grid)
+    assert coeffs == ctypes.sizeof(pdds.pdds_coeffs)
+    assert stats == ctypes.sizeof(pdds.pdds_stats_t)
