@@ -154,7 +154,8 @@ pdds_status pdds_get_launch(const pdds_ctx* ctx, int32_t* block, int32_t* ctas_p
 /* Autotuner: times short assemblies of a sample of the knots (every 8th, at
  * the full per-knot budget n_paths, time step dt) for every combination of
  * block in {128, 256, 512}, unit_paths in {1024, 4096, 16384} and exit_batch
- * in {2, 4, 8}, and keeps the fastest (ties to the first).  The launch shape
+ * in {2, 4, 8}, twice each; the four fastest are then timed twice on the whole
+ * problem (every knot at n_paths) and the fastest of those is kept.  The launch shape
  * only reorders floating-point additions, never the estimator.  Results are
  * cached for the process per (device, coefficient set, control variate on/off,
  * grid, n_paths); a cached shape is applied without timing.  Allocates and

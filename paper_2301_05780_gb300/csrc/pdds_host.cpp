@@ -753,23 +753,48 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   const int units[] = {1024, 4096, 16384};
   const int batches[] = {2, 4, 8};
   Shape best{c->block, (int)c->unit_paths, c->exit_batch};
-  float best_ms = 1e30f;
   c->timing = true;
   c->ctas_per_sm = 0;
+  // two interleaved rounds; a shape's time is its faster round (a single
+  // timing of a few milliseconds is noisy at the 2-3 % level that separates
+  // the best shapes)
+  std::vector<Shape> shapes;
   for (int bl : blocks)
     for (int un : units)
-      for (int ba : batches) {
-        if (st != PDDS_OK) break;
-        if (c->cv_on && bl > 256) continue;
-        c->block = bl;
-        c->unit_paths = un;
-        c->exit_batch = ba;
-        st = assemble_impl(c, dN, 0, dt, seed, &G, b, nullptr, s);
-        if (st == PDDS_OK && c->st.path_kernel_ms < best_ms) {
-          best_ms = c->st.path_kernel_ms;
-          best = Shape{bl, un, ba};
-        }
-      }
+      for (int ba : batches)
+        if (!(c->cv_on && bl > 256)) shapes.push_back(Shape{bl, un, ba});
+  std::vector<float> ms(shapes.size(), 1e30f);
+  for (int round = 0; round < 2 && st == PDDS_OK; ++round)
+    for (size_t i = 0; i < shapes.size() && st == PDDS_OK; ++i) {
+      c->block = shapes[i].block;
+      c->unit_paths = shapes[i].unit;
+      c->exit_batch = shapes[i].batch;
+      st = assemble_impl(c, dN, 0, dt, seed, &G, b, nullptr, s);
+      if (st == PDDS_OK) ms[i] = std::min(ms[i], c->st.path_kernel_ms);
+    }
+  // The sample's tail (few units left, lanes idle) weighs more than in the
+  // full problem, so the four best shapes of the sample are timed again, twice
+  // each, on the whole problem (every knot at n_paths), and the fastest wins.
+  std::vector<size_t> order(shapes.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b2) { return ms[a] < ms[b2]; });
+  const size_t finalists = std::min<size_t>(4, order.size());
+  std::vector<float> full(finalists, 1e30f);
+  for (int round = 0; round < 2 && st == PDDS_OK; ++round)
+    for (size_t f = 0; f < finalists && st == PDDS_OK; ++f) {
+      const Shape& sh = shapes[order[f]];
+      c->block = sh.block;
+      c->unit_paths = sh.unit;
+      c->exit_batch = sh.batch;
+      st = assemble_impl(c, nullptr, n_paths, dt, seed, &G, b, nullptr, s);
+      if (st == PDDS_OK) full[f] = std::min(full[f], c->st.path_kernel_ms);
+    }
+  float best_ms = 1e30f;
+  for (size_t f = 0; f < finalists; ++f)
+    if (full[f] < best_ms) {
+      best_ms = full[f];
+      best = shapes[order[f]];
+    }
   c->timing = timing;
   c->block = best.block;
   c->unit_paths = best.unit;

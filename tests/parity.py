@@ -41,11 +41,22 @@ def subtract_paths(raw_G, raw_b, rec, sel, rows_index, w_a="w_a", w_b="w_b"):
         raw_b[r] -= rec["b_contrib"][i]
 
 
-def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None):
+def fp32_path_atol(L, mean_steps, spacing):
+    """Absolute floor, in per-path weight units, for FP32 paths on large
+    patches: a position kept in FP32 relative to its knot (|X| <= L) rounds by
+    at most 2^-24 L per step; over K steps the rounding walks ~2^-24 L sqrt(K),
+    i.e. 2^-24 L sqrt(K) / spacing of an interpolation weight.  Eight times
+    that (both coordinates, a 4-sigma margin) and never below ATOL_RAW."""
+    return max(ATOL_RAW, 8.0 * 2.0 ** -24 * L * np.sqrt(mean_steps) / spacing)
+
+
+def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, atol_raw=None):
     """gpu/orc: dicts with row_ptr, col, val (finalized G), b, rec (records for
     `rows` in order, Nk[r] paths each).  b_extra_tol (per row, raw units) widens
     the b bound where part of b is computed at lower precision on purpose (the
-    BF16 control variate).  Returns the flagged fraction."""
+    BF16 control variate).  atol_raw (per-path units; default ATOL_RAW) is the
+    floor of fp32_path_atol for large patches; it scales with the square root
+    of the number of path weights in an entry.  Returns the flagged fraction."""
     Nk = np.asarray(Nk, dtype=np.int64)
     rows_index = np.repeat(np.arange(len(rows)), Nk)
     rg, ro = gpu["rec"], orc["rec"]
@@ -65,13 +76,19 @@ def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None):
     subtract_paths(Gg, bg, rg, flag, rows_index)
     subtract_paths(Go, bo, ro, flag, rows_index)
     err = np.abs(Gg - Go)
-    bad = err > RTOL * np.abs(Go) + ATOL_RAW
+    if atol_raw is None:
+        atol_g = ATOL_RAW
+        atol_b = ATOL_RAW
+    else:
+        atol_g = atol_raw * np.maximum(1.0, np.sqrt(np.abs(Go)))
+        atol_b = atol_raw * np.sqrt(np.asarray(Nk, dtype=np.float64))
+    bad = err > RTOL * np.abs(Go) + atol_g
     assert not bad.any(), (f"G mismatch at {np.argwhere(bad)[:5].tolist()}: gpu "
                            f"{Gg[bad][:5]} oracle {Go[bad][:5]}")
     babs = np.bincount(rows_index[~flag], weights=np.abs(ro["b_contrib"][~flag]),
                        minlength=len(rows))
     berr = np.abs(bg - bo)
     extra = 0.0 if b_extra_tol is None else np.asarray(b_extra_tol)
-    bbad = berr > RTOL * babs + ATOL_RAW + extra
+    bbad = berr > RTOL * babs + atol_b + extra
     assert not bbad.any(), f"b mismatch rows {np.nonzero(bbad)[0][:5]}: {bg[bbad]} vs {bo[bbad]}"
     return frac

@@ -310,7 +310,9 @@ def test_plan_bit_exact(orc):
 def test_paper_e1_sampled_rows(orc, scheme):
     """The Sec. 5.1 Poisson problem at the paper's size (11,241 knots,
     h = 0.08) with N = 200 paths per knot: eight sampled rows against the
-    oracle."""
+    oracle.  Patches are 40 wide and paths ~1000 steps long, so FP32 rounding
+    of the knot-relative position moves a weight by up to ~1e-4
+    (parity.fp32_path_atol sets the floor from those sizes)."""
     w = W.paper_e1().scaled(n_paths=200)
     g = run_gpu(w, scheme)
     n = len(g["b"])
@@ -318,7 +320,11 @@ def test_paper_e1_sampled_rows(orc, scheme):
     o = run_oracle(orc, w, orc.SCHEME_GM if scheme == GM else orc.SCHEME_EM, rows=rows)
     gr = dict(g)
     gr["rec"] = rows_of(g["rec"], rows, w.n_paths)
-    parity.compare_rows(gr, o, rows, np.full(rows.size, w.n_paths), n)
+    L = (w.grid["x1"] - w.grid["x0"]) / w.grid["Hx"]
+    mean_steps = o["stats"][0] / (rows.size * w.n_paths)
+    atol = parity.fp32_path_atol(L, mean_steps, L / w.grid["m"])
+    frac = parity.compare_rows(gr, o, rows, np.full(rows.size, w.n_paths), n, atol_raw=atol)
+    print(f"E1 scheme {scheme}: mean steps {mean_steps:.0f}, atol {atol:.2e}, flagged {frac:.2e}")
 
 
 def _e1_exact(xy):
