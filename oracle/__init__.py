@@ -32,6 +32,9 @@ COEF_CONSTANT = 4
 COEF_POISSON_E1 = 5
 SCHEME_EM = 0
 SCHEME_GM = 1
+INTERP_LINEAR = 0
+INTERP_RBF = 1
+MAX_STENCIL = 1024
 GM_SHIFT = 0.5826
 CAL_NMOM = 8
 MLP_NPARAM = 64 * 2 + 64 + 64 * 64 + 64 + 64 + 1
@@ -65,7 +68,8 @@ class Coeffs(C.Structure):
 
 RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side", "<i4"), ("flags", "<i4"),
                          ("col_a", "<i4"), ("col_b", "<i4"), ("pad_", "<i4"),
-                         ("w_a", "<f8"), ("w_b", "<f8"), ("b_contrib", "<f8"), ("Y", "<f8")])
+                         ("w_a", "<f8"), ("w_b", "<f8"), ("b_contrib", "<f8"), ("Y", "<f8"),
+                         ("s_line", "<f8")])
 
 
 CAL_RECORD_DTYPE = np.dtype([("steps_gm", "<i4"), ("side_gm", "<i4"), ("flags_gm", "<i4"),
@@ -77,7 +81,8 @@ CAL_RECORD_DTYPE = np.dtype([("steps_gm", "<i4"), ("side_gm", "<i4"), ("flags_gm
 class Run(C.Structure):
     _fields_ = [("n_per_knot", C.c_void_p), ("n_paths", C.c_int64), ("dt", C.c_double),
                 ("h_per_knot", C.c_void_p), ("k_max", C.c_int64), ("seed", C.c_uint64),
-                ("tag_word", C.c_uint32), ("scheme", C.c_int32)]
+                ("tag_word", C.c_uint32), ("scheme", C.c_int32), ("interp", C.c_int32),
+                ("pad_", C.c_int32), ("rbf_c", C.c_double)]
 
 
 def lib():
@@ -97,6 +102,11 @@ def lib():
             L.orc_calibrate.argtypes = [P, P, P, P, P, C.c_int32, C.c_int32, P, P, P]
             L.orc_plan.argtypes = [C.c_int64, P, C.c_double, C.c_double, C.c_double, C.c_int64,
                                    P, P, P]
+            L.orc_rbf_cardinal.argtypes = [C.c_int32, C.c_double, C.c_double, P]
+            L.orc_rbf_cond.argtypes = [C.c_int32, C.c_double]
+            L.orc_rbf_cond.restype = C.c_double
+            L.orc_rbf_shape_for_cond.argtypes = [C.c_int32, C.c_double]
+            L.orc_rbf_shape_for_cond.restype = C.c_double
             L.orc_finalize_rows.argtypes = [P, P, P, P, C.c_int64, P, C.c_int32, P, P]
             L.orc_coeffs_eval.argtypes = [P, P, C.c_double, C.c_double, P, P, P, P, P]
             L.orc_boundary_g.argtypes = [P, C.c_double, C.c_double]
@@ -160,7 +170,8 @@ class Problem:
             assert self._mlp.size == MLP_NPARAM
             self.coef.mlp = self._mlp.ctypes.data
 
-    def _run(self, n_paths, dt, seed, k_max, tag, scheme, h_per_knot):
+    def _run(self, n_paths, dt, seed, k_max, tag, scheme, h_per_knot, interp=INTERP_LINEAR,
+             rbf_c=0.0):
         per = None
         N = 0
         if np.ndim(n_paths) == 0:
@@ -173,11 +184,12 @@ class Problem:
             h = np.ascontiguousarray(h_per_knot, dtype=np.float64)
             assert h.size == self.n
         run = Run(_p(per), N, float(dt), _p(h), int(k_max), int(seed) & (2**64 - 1),
-                  int(tag) & 0xffffffff, int(scheme))
+                  int(tag) & 0xffffffff, int(scheme), int(interp), 0, float(rbf_c))
         return run, per, N, h
 
     def assemble(self, n_paths, dt, seed, k_max, rows=None, threads=None, tag=0,
-                 records=False, finalize=True, scheme=SCHEME_EM, h_per_knot=None):
+                 records=False, finalize=True, scheme=SCHEME_EM, h_per_knot=None,
+                 interp=INTERP_LINEAR, rbf_c=0.0):
         """Rows of G (CSR values in this object's pattern) and b (Eq. 24-25).
 
         n_paths is an int (all knots) or an int64 array of length n; h_per_knot
@@ -187,7 +199,8 @@ class Problem:
         if rows is None:
             rows = np.arange(self.n, dtype=np.int32)
         rows = np.ascontiguousarray(rows, dtype=np.int32)
-        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, scheme, h_per_knot)
+        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, scheme, h_per_knot, interp,
+                                   rbf_c)
         threads = int(threads or os.cpu_count() or 1)
         val = np.zeros(max(self.nnz, 1))[: self.nnz]
         b = np.zeros(self.n)
@@ -304,6 +317,22 @@ def mlp_loss_grad(theta, xy, target):
     g = np.zeros(MLP_NPARAM)
     loss = lib().orc_mlp_loss_grad(_p(theta), _p(xy), _p(target), target.size, _p(g))
     return loss, g
+
+
+def rbf_cardinal(m, c_lat, z):
+    """H_0..H_{m-1}(z) of the IMQ RBF on the stencil 0..m-1 (lattice units)."""
+    H = np.zeros(int(m))
+    if lib().orc_rbf_cardinal(int(m), float(c_lat), float(z), _p(H)) != 0:
+        raise ValueError("oracle: bad RBF stencil")
+    return H
+
+
+def rbf_cond(m, c_lat):
+    return lib().orc_rbf_cond(int(m), float(c_lat))
+
+
+def rbf_shape_for_cond(m, cond):
+    return lib().orc_rbf_shape_for_cond(int(m), float(cond))
 
 
 def plan(moments, eps, h0, h0p, n_job):

@@ -418,15 +418,179 @@ typedef struct {
   uint32_t key[2];
   uint32_t tag;
   int64_t k_max;
+  int interp;                /* ORC_INTERP_*                                     */
+  double rbf_c;              /* IMQ shape parameter (absolute units)              */
+  struct rbf_cache_s* rbf[2];/* factorised RBF matrices: [0] lines along x,
+                                [1] lines along y (lattice spacing dx, dy)       */
 } sim_t;
+
+/* ========================================================================= *
+ * 1-D RBF interpolation on a stencil (Sec. 2.1, Eq. 1-5) with the inverse     *
+ * multiquadric phi_c(r) = 1 / sqrt(r^2 + c^2) (Eq. 3, read with + c^2).        *
+ * On an equispaced stencil of m points the cardinal functions, in lattice     *
+ * units, depend only on m and c / spacing: H(z) = Phi^{-1} phi(z) with        *
+ * phi(z)_i = phi_c(|z - z_i|) (Eq. 5, Phi symmetric), computed by LU with      *
+ * partial pivoting in FP64.                                                   *
+ * ========================================================================= */
+typedef struct rbf_cache_s {
+  double c_lat;              /* shape parameter in lattice units                */
+  double* lu[ORC_MAX_STENCIL + 1];   /* LU factors of Phi for stencil length m  */
+  int* piv[ORC_MAX_STENCIL + 1];
+  pthread_mutex_t mu;
+} rbf_cache_t;
+
+static double imq(double r, double c) { return 1.0 / sqrt(r * r + c * c); }
+
+/* In-place LU with partial pivoting of the m x m row-major A; 0 or -1 if singular. */
+static int lu_factor(int m, double* A, int* piv) {
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (fabs(A[(size_t)i * m + k]) > fabs(A[(size_t)p * m + k])) p = i;
+    piv[k] = p;
+    if (A[(size_t)p * m + k] == 0.0) return -1;
+    if (p != k)
+      for (int j = 0; j < m; ++j) {
+        double t = A[(size_t)k * m + j];
+        A[(size_t)k * m + j] = A[(size_t)p * m + j];
+        A[(size_t)p * m + j] = t;
+      }
+    for (int i = k + 1; i < m; ++i) {
+      double l = A[(size_t)i * m + k] / A[(size_t)k * m + k];
+      A[(size_t)i * m + k] = l;
+      for (int j = k + 1; j < m; ++j) A[(size_t)i * m + j] -= l * A[(size_t)k * m + j];
+    }
+  }
+  return 0;
+}
+
+static void lu_solve_inplace(int m, const double* LU, const int* piv, double* x) {
+  /* whole rows (multipliers included) were swapped: P A = L U */
+  for (int k = 0; k < m; ++k)
+    if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+  for (int k = 0; k < m; ++k)
+    for (int i = k + 1; i < m; ++i) x[i] -= LU[(size_t)i * m + k] * x[k];
+  for (int i = m - 1; i >= 0; --i) {
+    double v = x[i];
+    for (int j = i + 1; j < m; ++j) v -= LU[(size_t)i * m + j] * x[j];
+    x[i] = v / LU[(size_t)i * m + i];
+  }
+}
+
+static void rbf_matrix(int m, double c, double* A) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = imq((double)(i - j), c);
+}
+
+/* Cardinal functions H_0..H_{m-1} at z (lattice units from the first point). */
+static int rbf_eval(const double* LU, const int* piv, int m, double c, double z, double* H) {
+  for (int i = 0; i < m; ++i) H[i] = imq(z - (double)i, c);
+  lu_solve_inplace(m, LU, piv, H);
+  return 0;
+}
+
+static int rbf_get(rbf_cache_t* C, int m, const double** LU, const int** piv) {
+  pthread_mutex_lock(&C->mu);
+  if (!C->lu[m]) {
+    double* A = (double*)malloc((size_t)m * m * sizeof(double));
+    int* p = (int*)malloc((size_t)m * sizeof(int));
+    rbf_matrix(m, C->c_lat, A);
+    if (lu_factor(m, A, p)) { free(A); free(p); pthread_mutex_unlock(&C->mu); return -1; }
+    C->lu[m] = A;
+    C->piv[m] = p;
+  }
+  *LU = C->lu[m];
+  *piv = C->piv[m];
+  pthread_mutex_unlock(&C->mu);
+  return 0;
+}
+
+static void rbf_cache_free(rbf_cache_t* C) {
+  if (!C) return;
+  for (int m = 0; m <= ORC_MAX_STENCIL; ++m) { free(C->lu[m]); free(C->piv[m]); }
+  pthread_mutex_destroy(&C->mu);
+  free(C);
+}
+
+int orc_rbf_cardinal(int32_t m, double c_lat, double z, double* H) {
+  if (m < 2 || m > ORC_MAX_STENCIL || !(c_lat > 0)) return -1;
+  double* A = (double*)malloc((size_t)m * m * sizeof(double));
+  int* p = (int*)malloc((size_t)m * sizeof(int));
+  rbf_matrix(m, c_lat, A);
+  int rc = lu_factor(m, A, p);
+  if (!rc) rbf_eval(A, p, m, c_lat, z, H);
+  free(A);
+  free(p);
+  return rc;
+}
+
+/* Eigenvalues of the symmetric m x m matrix A (destroyed) by cyclic Jacobi
+ * rotations; returns the spectral condition number max|l| / min|l|. */
+static double sym_cond(int m, double* A) {
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+    if (off < 1e-300) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        double apq = A[(size_t)p * m + q];
+        if (fabs(apq) < 1e-300) continue;
+        double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+        double th = (aqq - app) / (2.0 * apq);
+        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < m; ++k) {
+          double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = cs * akp - sn * akq;
+          A[(size_t)k * m + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = cs * apk - sn * aqk;
+          A[(size_t)q * m + k] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double lo = 1e300, hi = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double v = fabs(A[(size_t)i * m + i]);
+    if (v < lo) lo = v;
+    if (v > hi) hi = v;
+  }
+  return hi / lo;
+}
+
+double orc_rbf_cond(int32_t m, double c_lat) {
+  double* A = (double*)malloc((size_t)m * m * sizeof(double));
+  rbf_matrix(m, c_lat, A);
+  double k = sym_cond(m, A);
+  free(A);
+  return k;
+}
+
+/* The shape parameter (lattice units) at which the spectral condition number
+ * of Phi for an m-point stencil equals `cond` (Sec. 5.1 fixes c that way):
+ * bisection on log c, the condition number growing with c. */
+double orc_rbf_shape_for_cond(int32_t m, double cond) {
+  double lo = 1e-3, hi = 1e2;
+  for (int it = 0; it < 200; ++it) {
+    double mid = sqrt(lo * hi);
+    if (orc_rbf_cond(m, mid) < cond) lo = mid; else hi = mid;
+    if (hi / lo < 1.0 + 1e-12) break;
+  }
+  return sqrt(lo * hi);
+}
 
 typedef struct {
   int steps, side, flags;
-  int col[2];          /* unknown-knot columns, -1 if none */
-  double w[2];         /* Y * interpolation weight for col[]  */
+  int nw;                        /* entries used in col[] / w[]          */
+  int col[ORC_MAX_STENCIL];      /* unknown-knot columns, -1 if none     */
+  double w[ORC_MAX_STENCIL];     /* Y * interpolation weight for col[]   */
   double bsum;         /* everything that goes to b (Z + xi + Dirichlet terms) */
   double Y;
   double xi;           /* the control-variate integral alone (0 without one) */
+  double s_line;       /* exit coordinate along the side's line, lattice units */
 } path_out_t;
 
 typedef struct { double xlo, xhi, ylo, yhi; } box_t;
@@ -484,8 +648,10 @@ static void resolve_exit(const sim_t* S, const patch_t* P, const box_t* B, doubl
   out->steps = (int)n;
   out->side = side;
   out->flags = truncated ? 1 : 0;
+  out->nw = 2;
   out->col[0] = out->col[1] = -1;
   out->w[0] = out->w[1] = 0;
+  out->s_line = 0.0;
   out->Y = Yk;
   out->xi = xi;
   double bsum = Z + xi;
@@ -508,20 +674,49 @@ static void resolve_exit(const sim_t* S, const patch_t* P, const box_t* B, doubl
     double s = (along - origin) / step;
     if (s < P->a[side]) { s = P->a[side]; out->flags |= 2; }
     if (s > P->b[side]) { s = P->b[side]; out->flags |= 2; }
-    int t = (int)floor(s);
-    if (t >= P->b[side]) t = P->b[side] - 1;
-    double lam = s - t;
-    double w[2] = {1.0 - lam, lam};
-    for (int q = 0; q < 2; ++q) {
-      int tl = t + q;
-      int i = vertical ? P->line[side] : tl;
-      int j = vertical ? tl : P->line[side];
-      if (tl == 0 || tl == lmax) {
-        /* Stencil end on the boundary of Omega: known value g there. */
-        bsum += Yk * w[q] * orc_boundary_g(S->cf, g->x0 + i * G->dx, g->y0 + j * G->dy);
+    out->s_line = s;
+    if (S->interp == ORC_INTERP_RBF) {
+      /* Eq. 21-22: every stencil knot j gets the cardinal weight H_j(P). */
+      int m = P->b[side] - P->a[side] + 1;
+      const double* LU;
+      const int* piv;
+      double H[ORC_MAX_STENCIL];
+      rbf_cache_t* C = S->rbf[vertical ? 1 : 0];
+      if (rbf_get(C, m, &LU, &piv) == 0) {
+        rbf_eval(LU, piv, m, C->c_lat, s - P->a[side], H);
       } else {
-        out->col[q] = G->grid[(size_t)j * (G->LX + 1) + i];
-        out->w[q] = Yk * w[q];
+        for (int q = 0; q < m; ++q) H[q] = 0.0;
+      }
+      out->nw = m;
+      for (int q = 0; q < m; ++q) {
+        int tl = P->a[side] + q;
+        int i = vertical ? P->line[side] : tl;
+        int j = vertical ? tl : P->line[side];
+        out->col[q] = -1;
+        out->w[q] = 0.0;
+        if (tl == 0 || tl == lmax)
+          bsum += Yk * H[q] * orc_boundary_g(S->cf, g->x0 + i * G->dx, g->y0 + j * G->dy);
+        else {
+          out->col[q] = G->grid[(size_t)j * (G->LX + 1) + i];
+          out->w[q] = Yk * H[q];
+        }
+      }
+    } else {
+      int t = (int)floor(s);
+      if (t >= P->b[side]) t = P->b[side] - 1;
+      double lam = s - t;
+      double w[2] = {1.0 - lam, lam};
+      for (int q = 0; q < 2; ++q) {
+        int tl = t + q;
+        int i = vertical ? P->line[side] : tl;
+        int j = vertical ? tl : P->line[side];
+        if (tl == 0 || tl == lmax) {
+          /* Stencil end on the boundary of Omega: known value g there. */
+          bsum += Yk * w[q] * orc_boundary_g(S->cf, g->x0 + i * G->dx, g->y0 + j * G->dy);
+        } else {
+          out->col[q] = G->grid[(size_t)j * (G->LX + 1) + i];
+          out->w[q] = Yk * w[q];
+        }
       }
     }
   }
@@ -640,7 +835,7 @@ static void assemble_row(job_t* J, int r, int64_t* st) {
     st[0] += o.steps;
     st[1] += (o.flags & 1) ? 1 : 0;
     st[2] += (o.flags & 2) ? 1 : 0;
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < o.nw; ++q) {
       if (o.col[q] < 0) continue;
       int lo = 0, hi = nc - 1, pos = -1;       /* column search in the row */
       while (lo <= hi) {
@@ -655,8 +850,10 @@ static void assemble_row(job_t* J, int r, int64_t* st) {
     if (J->records) {
       orc_record* R = &J->records[J->rec_off[r] + p];
       R->steps = o.steps; R->side = o.side; R->flags = o.flags;
-      R->col_a = o.col[0]; R->col_b = o.col[1]; R->pad_ = 0;
-      R->w_a = o.w[0]; R->w_b = o.w[1]; R->b_contrib = o.bsum; R->Y = o.Y;
+      const int lin = J->S.interp != ORC_INTERP_RBF;  /* RBF: weights from s_line */
+      R->col_a = lin ? o.col[0] : -1; R->col_b = lin ? o.col[1] : -1; R->pad_ = 0;
+      R->w_a = lin ? o.w[0] : 0.0; R->w_b = lin ? o.w[1] : 0.0;
+      R->b_contrib = o.bsum; R->Y = o.Y; R->s_line = o.s_line;
     }
   }
   for (int q = 0; q < nc; ++q) J->val[rb + q] = acc[q];
@@ -695,6 +892,23 @@ static int job_begin(job_t* J, geom_t* G, const orc_grid* g, const orc_coeffs* c
   J->S.G = G; J->S.cf = cf; J->S.dt = run->dt; J->S.h_per_knot = run->h_per_knot;
   J->S.key[0] = (uint32_t)run->seed; J->S.key[1] = (uint32_t)(run->seed >> 32);
   J->S.tag = run->tag_word; J->S.k_max = run->k_max;
+  J->S.interp = run->interp;
+  J->S.rbf_c = run->rbf_c;
+  J->S.rbf[0] = J->S.rbf[1] = NULL;
+  if (run->interp == ORC_INTERP_RBF) {
+    if (!(run->rbf_c > 0) || 2 * g->m + 1 + 2 * g->ext > ORC_MAX_STENCIL) {
+      geom_free(G);
+      return -1;
+    }
+    for (int o = 0; o < 2; ++o) {
+      J->S.rbf[o] = (rbf_cache_t*)calloc(1, sizeof(rbf_cache_t));
+      J->S.rbf[o]->c_lat = run->rbf_c / (o == 0 ? G->dx : G->dy);
+      pthread_mutex_init(&J->S.rbf[o]->mu, NULL);
+    }
+  } else if (run->interp != ORC_INTERP_LINEAR) {
+    geom_free(G);
+    return -1;
+  }
   J->scheme = run->scheme;
   J->n_per_knot = run->n_per_knot; J->n_paths = run->n_paths;
   J->rows = rows; J->nrows = nrows;
@@ -733,6 +947,8 @@ int orc_assemble_ex(const orc_grid* g, const orc_coeffs* cf, const orc_run* run,
   J.rec_off = off;
   job_run(&J, threads, stats);
   free(off);
+  rbf_cache_free(J.S.rbf[0]);
+  rbf_cache_free(J.S.rbf[1]);
   geom_free(&G);
   return 0;
 }
@@ -761,7 +977,7 @@ int orc_assemble(const orc_grid* g, const orc_coeffs* cf,
  * ========================================================================= */
 static double score_of(const path_out_t* o, const double* u0) {
   double phi = o->bsum - o->xi;
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < o->nw; ++q)
     if (o->col[q] >= 0) phi += o->w[q] * u0[o->col[q]];
   return phi;
 }
@@ -807,6 +1023,8 @@ int orc_calibrate(const orc_grid* g, const orc_coeffs* cf, const orc_run* run, c
   J.rec_off = off;
   job_run(&J, threads, stats);
   free(off);
+  rbf_cache_free(J.S.rbf[0]);
+  rbf_cache_free(J.S.rbf[1]);
   geom_free(&G);
   return 0;
 }

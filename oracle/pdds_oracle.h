@@ -29,6 +29,11 @@
  *                                  systems applied to u0, constant data give
  *                                  zero variance, v = 0 gives rho = 0
  *   orc_plan               pinned: Eq. 40-41 on hand-worked values
+ *   RBF stencils (orc_rbf_*, ORC_INTERP_RBF)
+ *                          pinned: cardinal property, a library RBF
+ *                                  interpolator on the same points, spectral
+ *                                  accuracy on smooth data, the assembled
+ *                                  weights against the cardinal functions
  *   POISSON_E1 coefficients pinned: f against a finite-difference Laplacian
  *                                  of g = u of Eq. 43
  *   orc_mlp_*              pinned: finite differences, closed-form special cases
@@ -67,6 +72,14 @@ enum {
 };
 #define ORC_GM_SHIFT 0.5826
 
+/* Interpolation on the patch-side stencils (Eq. 21). */
+enum {
+  ORC_INTERP_LINEAR = 0,       /* piecewise linear (footnote 8)                   */
+  ORC_INTERP_RBF = 1           /* 1-D inverse-multiquadric RBF cardinal functions
+                                  over the whole stencil (Sec. 2.1, Eq. 1-5)        */
+};
+#define ORC_MAX_STENCIL 1024
+
 typedef struct {
   double x0, x1, y0, y1; /* Omega = [x0,x1] x [y0,y1]                              */
   int32_t Hx, Hy;        /* subdomain grid                                          */
@@ -91,9 +104,10 @@ typedef struct {
   int32_t flags;         /* bit0 truncated at k_max, bit1 along-line clamp applied   */
   int32_t col_a, col_b;  /* knot columns receiving w_a, w_b (-1: none / Dirichlet)    */
   int32_t pad_;
-  double w_a, w_b;       /* Y_K * interpolation weight                               */
+  double w_a, w_b;       /* Y_K * interpolation weight (linear; 0 for RBF)           */
   double b_contrib;      /* Z_K + xi_K + Dirichlet terms (goes to b)                 */
   double Y;              /* Y_K = exp(S_K)                                           */
+  double s_line;         /* interface exit: lattice coordinate along the side's line */
 } orc_record;
 
 /* One path of the mixed GM/EM calibration run (optional output). */
@@ -117,6 +131,9 @@ typedef struct {
   uint64_t seed;
   uint32_t tag_word;
   int32_t scheme;             /* ORC_SCHEME_* (orc_assemble_ex only)            */
+  int32_t interp;             /* ORC_INTERP_*                                   */
+  int32_t pad_;
+  double rbf_c;               /* IMQ shape parameter c (absolute units), RBF only */
 } orc_run;
 
 #define ORC_MLP_HIDDEN 64
@@ -164,6 +181,15 @@ int orc_calibrate(const orc_grid* g, const orc_coeffs* cf, const orc_run* run, c
  * rho^2(phi_GM, xi) (diag may be NULL). */
 void orc_plan(int64_t n, const double* moments, double eps, double h0, double h0p,
               int64_t n_job, double* h_out, int64_t* n_out, double* diag);
+
+/* Cardinal functions H_0..H_{m-1} (Eq. 5) of the IMQ RBF (Eq. 3 read with
+ * + c^2) on the stencil 0, 1, ..., m-1 (lattice units) at z; c_lat is the
+ * shape parameter in lattice units.  0, or -1 for a bad size or singular Phi. */
+int orc_rbf_cardinal(int32_t m, double c_lat, double z, double* H);
+/* Spectral condition number of Phi for that stencil (Jacobi eigenvalues). */
+double orc_rbf_cond(int32_t m, double c_lat);
+/* c_lat at which that condition number equals `cond` (bisection). */
+double orc_rbf_shape_for_cond(int32_t m, double cond);
 
 /* Finalize: the raw sums in val/b for the given rows become Eq. 24-25 entries. */
 void orc_finalize_rows(const orc_grid* g, const int64_t* row_ptr, const int32_t* col,
