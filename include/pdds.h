@@ -106,7 +106,10 @@ typedef struct {
   float b_contrib;    /* Z_K + xi_K + boundary terms: the path's share of b_k times N */
   float Y;            /* Y_K = exp(int c dt)                                          */
   float xi;           /* xi_K alone (0 without a control variate)                     */
-  int32_t pad_;
+  float s_line;       /* interface exit: coordinate along the side's grid line, in
+                         lattice spacings from the line's start (0 on the boundary of
+                         Omega); with RBF stencils col_a = col_b = -1, w_a = w_b = 0 and
+                         the weights are H_j(s_line) of the side's stencil           */
 } pdds_path_record;
 
 typedef struct {
@@ -200,6 +203,26 @@ pdds_status pdds_assemble(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_pa
 pdds_status pdds_assemble_records(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_paths,
                                   double dt, uint64_t seed, pdds_csr* G, double* b,
                                   pdds_path_record* records, void* cuda_stream);
+
+/* Interpolation on the patch-side stencils (Eq. 21):
+ *  PDDS_INTERP_LINEAR  piecewise linear between the two nearest stencil knots
+ *                      (footnote 8; the default);
+ *  PDDS_INTERP_RBF     1-D inverse-multiquadric RBF interpolation over the whole
+ *                      stencil (Sec. 2.1, Eq. 1-5, phi_c(r) = 1/sqrt(r^2 + c^2)):
+ *                      an exit at z gives every stencil knot j the weight Y H_j(z),
+ *                      H_j the cardinal functions (Eq. 5).  The library tabulates
+ *                      the H_j of every stencil length as per-interval Chebyshev
+ *                      series (FP64 construction, FP32 coefficients, truncation error
+ *                      below 2e-7 max|H|) and evaluates them at each exit.
+ * rbf_shape: c in the units of Omega; <= 0 picks the c at which the spectral
+ * condition number of the longest stencil's matrix Phi is 1e10 (the choice of
+ * Sec. 5.1).  shape_used / table_err (nullable, host): the c in use and the
+ * tables' truncation bound.  Applies to later assemble / calibrate calls on ctx
+ * (not to batches); synchronizes.  Errors: EINVAL (kind, or Phi not positive
+ * definite in FP64 for a too-large c), ENOMEM, ECUDA. */
+enum { PDDS_INTERP_LINEAR = 0, PDDS_INTERP_RBF = 1 };
+pdds_status pdds_set_interpolation(pdds_ctx* ctx, int32_t kind, double rbf_shape,
+                                   double* shape_used, double* table_err);
 
 /* Exit scheme of the path kernel (Sec. 2.3):
  *  PDDS_SCHEME_EM  naive Euler-Maruyama: exit at the first step outside the

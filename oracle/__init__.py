@@ -219,7 +219,7 @@ class Problem:
         return val, b, stats, rec
 
     def calibrate(self, u0, n_paths, dt, seed, k_max, rows=None, threads=None, tag=0,
-                  records=False, h_per_knot=None):
+                  records=False, h_per_knot=None, interp=INTERP_LINEAR, rbf_c=0.0):
         """Mixed GM/EM calibration run (Sec. 4.1) with the nodal u0 as patch data.
 
         Returns (moments [len(rows), CAL_NMOM], stats, records-or-None)."""
@@ -229,7 +229,8 @@ class Problem:
         rows = np.ascontiguousarray(rows, dtype=np.int32)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         assert u0.size == self.n
-        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, SCHEME_EM, h_per_knot)
+        run, per, N, h = self._run(n_paths, dt, seed, k_max, tag, SCHEME_EM, h_per_knot, interp,
+                                   rbf_c)
         threads = int(threads or os.cpu_count() or 1)
         mom = np.zeros((rows.size, CAL_NMOM))
         stats = np.zeros(3, dtype=np.int64)

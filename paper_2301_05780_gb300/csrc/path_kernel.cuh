@@ -35,6 +35,7 @@
 #include "pdds.h"
 #include "pdds_internal.h"
 #include "pdds_mlp.cuh"
+#include "pdds_rbf.cuh"
 
 namespace pdds {
 namespace {
@@ -535,8 +536,8 @@ __device__ void flush_unit(const Smem& S, int s, const KParams& P) {
   for (int i = lane; i < H.kd.nslots; i += 32) {
     const unsigned long long q = acc[i];
     const int c = __ldg(map + i);
-    // exact: q < 2^53, times a power of two
-    if (q != 0ull && c >= 0) atomicAdd(D.Gval + c, (double)q * kFixedInv);
+    // exact: |q| < 2^53, times a power of two (RBF weights may be negative)
+    if (q != 0ull && c >= 0) atomicAdd(D.Gval + c, (double)(long long)q * kFixedInv);
   }
   if (lane == 0) atomicAdd(D.b + H.k, H.bsum);
   __syncwarp();
@@ -771,6 +772,11 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
     // ---- resolve the exits (Eq. 22-25, corner rule of Sec. 3.3) -----------
     const bool leaving = alive && exited;
     double bc = 0.0;
+    int side = 0, flags = 0;
+    float Yk = 1.0f, sl = 0.f, s_line = 0.f;
+    int col_a = -1, col_b = -1;
+    float wa = 0.f, wb = 0.f;
+    bool rbf_exit = false;  // EXT + RBF stencils: weights come from the warp loop below
     if (leaving) {
       const Stage& H = S.st(st);
       const KnotDesc& kd = H.kd;
@@ -790,7 +796,7 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
           ov[3] = (tb[2] + sh[3]) - Y;
         }
       }
-      int side = -1;
+      side = -1;
 #pragma unroll
       for (int o = 0; o < 4; ++o)
         if (ov[o] > 0.f && (side < 0 || ov[o] < ov[side])) side = o;
@@ -799,14 +805,11 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
         for (int o = 0; o < 4; ++o)
           if (side < 0 || ov[o] > ov[side]) side = o;
       }
-      float Yk = 1.0f;
       if constexpr (has_c<COEF>()) Yk = __expf(Sx);
       bc = (double)Z;
       if constexpr (CV) bc += (double)XI;
       const bool vertical = (side == 0 || side == 2);
-      int flags = trunc ? 1 : 0;
-      int col_a = -1, col_b = -1;
-      float wa = 0.f, wb = 0.f;
+      flags = trunc ? 1 : 0;
       if ((kd.dirbits >> side) & 1) {
         // exit on the boundary of Omega: Y g at the normal projection
         float along = vertical ? (yk + Y) : (xk + X);
@@ -815,56 +818,106 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
                                     : fmaf((float)kd.line[side], H.dy, H.y0);
         bc += (double)Yk * (double)g_value<COEF>(H, vertical ? line : along, vertical ? along : line);
       } else {
-        // exit on an interface: linear interpolation on the extended stencil
+        // exit on an interface: interpolation on the side's extended stencil
         const int a = kd.a[side], b = kd.b[side];
         const int kal = vertical ? kd.kj : kd.ki;
-        float sl = (float)(kal - a) + (vertical ? Y * H.inv_dy : X * H.inv_dx);
+        sl = (float)(kal - a) + (vertical ? Y * H.inv_dy : X * H.inv_dx);
         const float smax = (float)(b - a);
         if (sl < 0.f) { sl = 0.f; flags |= 2; }
         if (sl > smax) { sl = smax; flags |= 2; }
-        int t = (int)floorf(sl);
-        if (t >= b - a) t = b - a - 1;
-        const float lam = sl - (float)t;
-        // Y (1 - lam) and Y lam in 2^-30 units: q0 + q1 = qY exactly, so the
-        // path deposits its whole weight Y on the two knots (G 1 = b holds
-        // exactly when c = f = 0 and g = 1).
-        const unsigned long long qY = __float2ull_rn(Yk * kFixedOne);
-        const unsigned long long q1 = __float2ull_rn((Yk * lam) * kFixedOne);
-        const unsigned long long qw[2] = {qY - q1, q1};
-        const int lmax = vertical ? H.LY : H.LX;
+        s_line = (float)a + sl;
+        if constexpr (EXT) rbf_exit = prob_desc(P, H.prob).rbf_coef != nullptr;
+        if (!rbf_exit) {
+          // linear: the two nearest stencil knots
+          int t = (int)floorf(sl);
+          if (t >= b - a) t = b - a - 1;
+          const float lam = sl - (float)t;
+          // Y (1 - lam) and Y lam in 2^-30 units: q0 + q1 = qY exactly, so the
+          // path deposits its whole weight Y on the two knots (G 1 = b holds
+          // exactly when c = f = 0 and g = 1).
+          const unsigned long long qY = __float2ull_rn(Yk * kFixedOne);
+          const unsigned long long q1 = __float2ull_rn((Yk * lam) * kFixedOne);
+          const unsigned long long qw[2] = {qY - q1, q1};
+          const int lmax = vertical ? H.LY : H.LX;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int tl = a + t + q;
-          if (tl == 0 || tl == lmax) {
-            const int li = vertical ? kd.line[side] : tl;
-            const int lj = vertical ? tl : kd.line[side];
-            bc += (double)qw[q] * kFixedInv *
-                  (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0), fmaf((float)lj, H.dy, H.y0));
-          } else {
-            const int slot = kd.off[side] + t + q;
-            atomicAdd(acc + slot, qw[q]);
-            if constexpr (RECORD) {
-              const ProbDesc& D = prob_desc(P, H.prob);
-              const int c = D.slot2csr[kd.slot_base + slot];
-              const int col = D.col[c];
-              const float wv = (float)((double)qw[q] * kFixedInv);
-              if (q == 0) { col_a = col; wa = wv; }
-              else { col_b = col; wb = wv; }
+          for (int q = 0; q < 2; ++q) {
+            const int tl = a + t + q;
+            if (tl == 0 || tl == lmax) {
+              const int li = vertical ? kd.line[side] : tl;
+              const int lj = vertical ? tl : kd.line[side];
+              bc += (double)qw[q] * kFixedInv *
+                    (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
+                                          fmaf((float)lj, H.dy, H.y0));
+            } else {
+              const int slot = kd.off[side] + t + q;
+              atomicAdd(acc + slot, qw[q]);
+              if constexpr (RECORD) {
+                const ProbDesc& D = prob_desc(P, H.prob);
+                const int c = D.slot2csr[kd.slot_base + slot];
+                const int col = D.col[c];
+                const float wv = (float)((double)qw[q] * kFixedInv);
+                if (q == 0) { col_a = col; wa = wv; }
+                else { col_b = col; wb = wv; }
+              }
             }
           }
         }
       }
+    }
+    if constexpr (EXT) {
+      // RBF stencils (Eq. 21-22): every knot j of the exit side's stencil gets
+      // Y H_j(s).  The whole warp serves one exiting lane at a time, a knot per
+      // lane, evaluating the tabulated cardinal functions; knots on the
+      // boundary of Omega add Y H_j g(x_j) to the exiting lane's b share.
+      unsigned pend = __ballot_sync(kFull, rbf_exit);
+      while (pend) {
+        const int src = __ffs(pend) - 1;
+        const int r_st = __shfl_sync(kFull, st, src);
+        const int r_side = __shfl_sync(kFull, side, src);
+        const float r_s = __shfl_sync(kFull, sl, src);
+        const float r_Y = __shfl_sync(kFull, Yk, src);
+        const Stage& H = S.st(r_st);
+        const KnotDesc& kd = H.kd;
+        const ProbDesc& D = prob_desc(P, H.prob);
+        const bool vertical = (r_side == 0 || r_side == 2);
+        const int a = kd.a[r_side];
+        const int L = kd.b[r_side] - a + 1;
+        const int lmax = vertical ? H.LY : H.LX;
+        float tau;
+        const float* cf = rbf_interval(D, vertical ? 1 : 0, L, r_s, tau);
+        unsigned long long* acc = S.acc(r_st);
+        double dsum = 0.0;
+        for (int j = lane; j < L; j += 32) {
+          const float w = r_Y * rbf_cardinal(cf, L, D.rbf_deg + 1, j, tau);
+          const int tl = a + j;
+          if (tl == 0 || tl == lmax) {
+            const int li = vertical ? kd.line[r_side] : tl;
+            const int lj = vertical ? tl : kd.line[r_side];
+            dsum += (double)w * (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
+                                                      fmaf((float)lj, H.dy, H.y0));
+          } else {
+            // signed weights in 2^-30 units (two's complement in the slot)
+            atomicAdd(acc + kd.off[r_side] + j,
+                      (unsigned long long)__float2ll_rn(w * kFixedOne));
+          }
+        }
+        dsum = warp_sum(dsum);
+        if (lane == src) bc += dsum;
+        pend &= pend - 1;
+      }
+    }
+    if (leaving) {
       my_steps += (unsigned long long)n;
       my_paths += 1;
       my_trunc += (flags & 1);
       my_clamp += (flags >> 1) & 1;
       if constexpr (RECORD) {
-        const ProbDesc& D = prob_desc(P, H.prob);
+        const ProbDesc& D = prob_desc(P, S.st(st).prob);
         const int64_t idx = (D.path_prefix ? D.path_prefix[kk] : (int64_t)kk * D.n_paths) + p;
         PathRecordDev R;
         R.steps = n; R.side_flags = side | (flags << 8); R.col_a = col_a; R.col_b = col_b;
         R.w_a = wa; R.w_b = wb; R.b_contrib = (float)bc; R.Y = Yk;
-        R.xi = XI; R.pad_ = 0;
+        R.xi = XI; R.s_line = s_line;
         P.records[idx] = R;
       }
       atomicAdd(&S.st(st).bsum, bc);  // one FP64 shared atomic per exit

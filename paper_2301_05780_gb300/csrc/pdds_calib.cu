@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "pdds_internal.h"
+#include "pdds_rbf.cuh"
 
 namespace pdds {
 namespace {
@@ -25,10 +26,31 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNMom = 8;
 
-__device__ __forceinline__ double score(const PathRecordDev& r, const double* __restrict__ u0) {
+// phi of one path.  Linear stencils: the record's two weights.  RBF stencils
+// (D.rbf_coef set): Y H_j(s_line) on every unknown knot j of the exit side's
+// stencil (boundary knots are already in b_contrib), from the same tables the
+// path kernel used.
+__device__ __forceinline__ double score(const PathRecordDev& r, const double* __restrict__ u0,
+                                        const ProbDesc& D, const KnotDesc& kd) {
   double phi = (double)r.b_contrib - (double)r.xi;
   if (r.col_a >= 0) phi += (double)r.w_a * u0[r.col_a];
   if (r.col_b >= 0) phi += (double)r.w_b * u0[r.col_b];
+  const int side = r.side_flags & 0xFF;
+  if (D.rbf_coef != nullptr && !((kd.dirbits >> side) & 1)) {
+    const bool vertical = (side == 0 || side == 2);
+    const int a = kd.a[side];
+    const int L = kd.b[side] - a + 1;
+    float tau;
+    const float* cf = rbf_interval(D, vertical ? 1 : 0, L, r.s_line - (float)a, tau);
+    const int32_t* map = D.slot2csr + kd.slot_base + kd.off[side];
+    double acc = 0.0;
+    for (int j = 0; j < L; ++j) {
+      const int c = map[j];
+      if (c < 0) continue;
+      acc += (double)(r.Y * rbf_cardinal(cf, L, D.rbf_deg + 1, j, tau)) * u0[D.col[c]];
+    }
+    phi += acc;
+  }
   return phi;
 }
 
@@ -36,17 +58,18 @@ __global__ void calib_moments_kernel(const PathRecordDev* __restrict__ em,
                                      const PathRecordDev* __restrict__ gm,
                                      const int64_t* __restrict__ path_prefix, int64_t n_paths,
                                      const double* __restrict__ u0, int64_t n,
-                                     double* __restrict__ mom) {
+                                     double* __restrict__ mom, const ProbDesc D) {
   const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
   const int64_t beg = path_prefix ? path_prefix[k] : k * n_paths;
   const int64_t end = path_prefix ? path_prefix[k + 1] : beg + n_paths;
   double m[kNMom] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const KnotDesc& kd = D.knots[k];
   for (int64_t i = beg + lane; i < end; i += 32) {
     const PathRecordDev a = em[i];
     const PathRecordDev b = gm[i];
-    const double pe = score(a, u0), pg = score(b, u0), x = (double)b.xi;
+    const double pe = score(a, u0, D, kd), pg = score(b, u0, D, kd), x = (double)b.xi;
     const double d = pe - pg;
     m[1] += d;
     m[2] += d * d;
@@ -108,11 +131,12 @@ __global__ void plan_kernel(const double* __restrict__ mom, int64_t n, double ep
 
 cudaError_t launch_calib_moments(const PathRecordDev* rec_em, const PathRecordDev* rec_gm,
                                  const int64_t* path_prefix, int64_t n_paths, const double* u0,
-                                 int64_t n, double* moments, cudaStream_t stream) {
+                                 int64_t n, double* moments, const ProbDesc& D,
+                                 cudaStream_t stream) {
   const int threads = 256;
   const int64_t blocks = (n * 32 + threads - 1) / threads;
   calib_moments_kernel<<<(unsigned)blocks, threads, 0, stream>>>(rec_em, rec_gm, path_prefix,
-                                                                   n_paths, u0, n, moments);
+                                                                   n_paths, u0, n, moments, D);
   return cudaGetLastError();
 }
 

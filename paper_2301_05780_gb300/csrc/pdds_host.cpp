@@ -247,6 +247,12 @@ struct pdds_ctx {
   int scheme = PDDS_SCHEME_EM;
   double* d_hknot = nullptr;  // owned copy of h_k, or nullptr
   double h_min = 0;           // smallest h_k (wait bound)
+  // stencil interpolation: linear, or RBF with device tables
+  int interp = PDDS_INTERP_LINEAR;
+  double rbf_shape = 0;
+  float* d_rbf_coef = nullptr;
+  int64_t* d_rbf_off = nullptr;
+  int rbf_deg = 0, rbf_lmax = 0;
   // calibration scratch: records of the naive and the GM pass, a CSR and b
   pdds_path_record* cal_rec = nullptr;
   int64_t cal_rec_cap = 0;    // records per pass
@@ -289,6 +295,7 @@ void free_ctx(pdds_ctx* c) {
   cudaFree(c->d_mlp);
   cudaFree(c->d_hknot); cudaFree(c->cal_rec); cudaFree(c->cal_val); cudaFree(c->cal_b);
   cudaFree(c->cal_rp); cudaFree(c->cal_col);
+  cudaFree(c->d_rbf_coef); cudaFree(c->d_rbf_off);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -336,6 +343,12 @@ ProbDesc make_prob(const pdds_ctx* c, int tag) {
   D.tag = tag;
   D.sigma_max = (float)(c->s_max * (1.0 + 1e-6));  // bilinear lookups may round up 1 ulp
   D.h_per_knot = c->d_hknot;
+  if (c->interp == PDDS_INTERP_RBF) {
+    D.rbf_coef = c->d_rbf_coef;
+    D.rbf_off = c->d_rbf_off;
+    D.rbf_deg = c->rbf_deg;
+    D.rbf_lmax = c->rbf_lmax;
+  }
   D.knots = c->d_knots;
   D.slot2csr = c->d_slot2csr;
   D.col = c->d_col;
@@ -451,7 +464,7 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   CK(c, pdds::launch_prob_prefix_single(D, c->d_prob_prefix, s));
   ++launches;
   const bool gm = (scheme < 0 ? c->scheme : scheme) == PDDS_SCHEME_GM;
-  const bool ext = gm || c->d_hknot != nullptr;
+  const bool ext = gm || c->d_hknot != nullptr || c->interp == PDDS_INTERP_RBF;
   if (pdds_status e = run_paths(c, D, nullptr, 1, dt, seed, kmax,
                                 reinterpret_cast<pdds::PathRecordDev*>(rec), s, stage_bytes(c),
                                 c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id, ext, gm))
@@ -860,6 +873,64 @@ pdds_status pdds_set_knot_steps(pdds_ctx* c, const double* h) {
   return PDDS_OK;
 }
 
+pdds_status pdds_set_interpolation(pdds_ctx* c, int32_t kind, double shape, double* shape_used,
+                                   double* table_err) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_interpolation: NULL context");
+  (void)cudaGetLastError();
+  if (kind == PDDS_INTERP_LINEAR) {
+    c->interp = kind;
+    if (shape_used) *shape_used = 0;
+    if (table_err) *table_err = 0;
+    return PDDS_OK;
+  }
+  if (kind != PDDS_INTERP_RBF)
+    return fail(c, PDDS_EINVAL, "set_interpolation: kind must be PDDS_INTERP_LINEAR or _RBF");
+  if (!std::isfinite(shape)) return fail(c, PDDS_EINVAL, "set_interpolation: shape not finite");
+  // stencil lengths per orientation (0: lines along x, sides N/S; 1: along y, E/W)
+  std::vector<int> len[2];
+  int lmax_any = 0;
+  for (const KnotDesc& d : c->geo.kd)
+    for (int o = 0; o < 4; ++o) {
+      if ((d.dirbits >> o) & 1) continue;
+      const int L = d.b[o] - d.a[o] + 1;
+      const int orient = (o == 0 || o == 2) ? 1 : 0;
+      if (std::find(len[orient].begin(), len[orient].end(), L) == len[orient].end())
+        len[orient].push_back(L);
+      lmax_any = std::max(lmax_any, L);
+    }
+  const double sp[2] = {c->geo.dx, c->geo.dy};
+  double cabs = shape;
+  if (!(cabs > 0)) {
+    // Sec. 5.1: c such that cond(Phi) of the longest stencil is 1e10
+    if (lmax_any < 2) return fail(c, PDDS_EINVAL, "set_interpolation: no interface stencils");
+    cabs = pdds::rbf_shape_for_cond(lmax_any, 1e10) * std::min(sp[0], sp[1]);
+  }
+  const double c_lat[2] = {cabs / sp[0], cabs / sp[1]};
+  pdds::RbfTables T;
+  std::string err;
+  if (!pdds::rbf_build_tables(len, c_lat, T, err)) return fail(c, PDDS_EINVAL, "set_interpolation: " + err);
+  float* coef = nullptr;
+  int64_t* off = nullptr;
+  if (dalloc(&coef, T.coef.size()) != cudaSuccess || dalloc(&off, T.offset.size()) != cudaSuccess) {
+    cudaFree(coef);
+    cudaFree(off);
+    return fail(c, PDDS_ENOMEM, "set_interpolation: table allocation failed");
+  }
+  CK(c, cudaMemcpy(coef, T.coef.data(), T.coef.size() * 4, cudaMemcpyHostToDevice));
+  CK(c, cudaMemcpy(off, T.offset.data(), T.offset.size() * 8, cudaMemcpyHostToDevice));
+  cudaFree(c->d_rbf_coef);
+  cudaFree(c->d_rbf_off);
+  c->d_rbf_coef = coef;
+  c->d_rbf_off = off;
+  c->rbf_deg = T.degree;
+  c->rbf_lmax = T.lmax;
+  c->rbf_shape = cabs;
+  c->interp = PDDS_INTERP_RBF;
+  if (shape_used) *shape_used = cabs;
+  if (table_err) *table_err = T.max_err;
+  return PDDS_OK;
+}
+
 pdds_status pdds_calibrate(pdds_ctx* c, const double* u0, const int64_t* N, int64_t Nu, double dt,
                            uint64_t seed, double* moments, void* stream) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "calibrate: NULL context");
@@ -910,7 +981,8 @@ pdds_status pdds_calibrate(pdds_ctx* c, const double* u0, const int64_t* N, int6
     return e;
   CK(c, pdds::launch_calib_moments(reinterpret_cast<const pdds::PathRecordDev*>(rec_em),
                                    reinterpret_cast<const pdds::PathRecordDev*>(rec_gm),
-                                   N ? c->d_path_prefix : nullptr, Nu, u0, n, moments, s));
+                                   N ? c->d_path_prefix : nullptr, Nu, u0, n, moments,
+                                   make_prob(c, 0), s));
   CK(c, cudaStreamSynchronize(s));
   c->st.kernel_launches += launches + 1;
   c->st.path_kernel_ms += em_st.path_kernel_ms;
@@ -1055,10 +1127,10 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same device");
     if (c->cv_on)
       return fail(c0, PDDS_EINVAL, "assemble_batch: control variates are not supported in batches");
-    if (c->scheme != PDDS_SCHEME_EM || c->d_hknot)
+    if (c->scheme != PDDS_SCHEME_EM || c->d_hknot || c->interp != PDDS_INTERP_LINEAR)
       return fail(c0, PDDS_EINVAL,
-                  "assemble_batch: the Gobet-Menozzi scheme and per-knot steps are not supported "
-                  "in batches");
+                  "assemble_batch: the Gobet-Menozzi scheme, per-knot steps and RBF stencils "
+                  "are not supported in batches");
     if (pdds_status e = check_csr(c, G[i], b[i])) return fail(c0, e, c->err);
     if (!(N && N[i]) && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
       return fail(c0, PDDS_EINVAL, "assemble_batch: n_paths must be in [1, 2^31)");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace pdds {
 
@@ -58,6 +59,10 @@ struct ProbDesc {
   const int32_t* col;             // CSR column of each value (records mode)
   const double* h_per_knot;       // per-knot steps (extended-exit kernels), or nullptr
   float sigma_max;                // upper bound of s(x) over the closure of Omega
+  int32_t rbf_deg;                // RBF stencils: Chebyshev degree of the tables
+  const float* rbf_coef;          // RBF stencils (extended kernels), or nullptr: linear
+  const int64_t* rbf_off;         // [2][rbf_lmax + 1] table offset per (orientation, length)
+  int32_t rbf_lmax;
   int32_t pad1_;
 };
 
@@ -76,7 +81,7 @@ struct Scratch {
 struct PathRecordDev {
   int32_t steps, side_flags, col_a, col_b;
   float w_a, w_b, b_contrib, Y, xi;
-  int32_t pad_;
+  float s_line;  // interface exit: lattice coordinate along the side's line
 };
 static_assert(sizeof(PathRecordDev) == 40, "record layout of pdds_path_record");
 
@@ -126,11 +131,31 @@ cudaError_t launch_finalize(const int32_t* row_ptr, const int32_t* col, double* 
                             const int64_t* n_per_knot, int64_t n_paths, int64_t n,
                             cudaStream_t stream);
 
+// RBF stencil tables (pdds_rbf.cpp, host): Chebyshev coefficients of the
+// cardinal functions of every stencil length, per lattice interval.
+struct RbfTables {
+  int degree = 0;
+  int lmax = 0;
+  double max_err = 0;              // coefficient tail bound of the truncation
+  double hmax = 0;                 // max |H| seen
+  std::vector<float> coef;         // [(t * (degree + 1) + n) * L + j] per table
+  std::vector<int64_t> offset;     // [2][lmax + 1], -1 where absent
+};
+// lengths[o]: stencil lengths of lines along x (o = 0) and y (o = 1);
+// c_lat[o]: the shape parameter in units of that orientation's spacing.
+bool rbf_build_tables(const std::vector<int> lengths[2], const double c_lat[2], RbfTables& T,
+                      std::string& err);
+double rbf_shape_for_cond(int m, double cond);  // c (lattice units) with cond(Phi) = cond
+double rbf_cond(int m, double c_lat);
+
 // Calibration (pdds_calib.cu): per-knot moments of the mixed GM/EM scores
 // from the records of the naive and the Gobet-Menozzi pass, and Eq. 40-41.
+// With RBF stencils (D.rbf_coef set) a score's interface part is rebuilt from
+// the record's exit side and coordinate with the same tables.
 cudaError_t launch_calib_moments(const PathRecordDev* rec_em, const PathRecordDev* rec_gm,
                                  const int64_t* path_prefix, int64_t n_paths, const double* u0,
-                                 int64_t n, double* moments, cudaStream_t stream);
+                                 int64_t n, double* moments, const ProbDesc& D,
+                                 cudaStream_t stream);
 cudaError_t launch_plan(const double* moments, int64_t n, double eps, double h0, double h0p,
                         int64_t n_job, double* h_out, int64_t* n_out, double* diag,
                         cudaStream_t stream);

@@ -57,10 +57,11 @@ class pdds_stats_t(C.Structure):
 
 RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side_flags", "<i4"), ("col_a", "<i4"),
                          ("col_b", "<i4"), ("w_a", "<f4"), ("w_b", "<f4"), ("b_contrib", "<f4"),
-                         ("Y", "<f4"), ("xi", "<f4"), ("pad_", "<i4")])
+                         ("Y", "<f4"), ("xi", "<f4"), ("s_line", "<f4")])
 RECORD_BYTES = RECORD_DTYPE.itemsize  # 40, as pdds_path_record
 
 PDDS_SCHEME_EM, PDDS_SCHEME_GM = 0, 1
+PDDS_INTERP_LINEAR, PDDS_INTERP_RBF = 0, 1
 CAL_NMOM = 8
 
 # name -> (restype, argtypes); mirrors include/pdds.h
@@ -81,6 +82,7 @@ _SIGS = {
     "pdds_assemble_records": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P,
                                         _P]),
     "pdds_set_scheme": (C.c_int, [_P, C.c_int32]),
+    "pdds_set_interpolation": (C.c_int, [_P, C.c_int32, C.c_double, _P, _P]),
     "pdds_set_knot_steps": (C.c_int, [_P, _P]),
     "pdds_calibrate": (C.c_int, [_P, _P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P]),
     "pdds_plan": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64, _P, _P,
@@ -254,6 +256,16 @@ def pdds_assemble_records(ctx, G, b, records, n_paths=0, n_per_knot=None, dt=1e-
 def pdds_set_scheme(ctx, scheme: int):
     """PDDS_SCHEME_EM (naive exit) or PDDS_SCHEME_GM (Gobet-Menozzi shift)."""
     _check(lib().pdds_set_scheme(ctx, int(scheme)), ctx)
+
+
+def pdds_set_interpolation(ctx, kind: int, rbf_shape: float = 0.0):
+    """PDDS_INTERP_LINEAR or PDDS_INTERP_RBF (shape c in domain units; <= 0:
+    cond(Phi) = 1e10).  Returns (shape used, table truncation bound)."""
+    used = C.c_double()
+    err = C.c_double()
+    _check(lib().pdds_set_interpolation(ctx, int(kind), float(rbf_shape), C.byref(used),
+                                        C.byref(err)), ctx)
+    return used.value, err.value
 
 
 def pdds_set_knot_steps(ctx, h_per_knot):

@@ -50,13 +50,16 @@ def fp32_path_atol(L, mean_steps, spacing):
     return max(ATOL_RAW, 8.0 * 2.0 ** -24 * L * np.sqrt(mean_steps) / spacing)
 
 
-def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, atol_raw=None):
+def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, atol_raw=None,
+                 rbf=None):
     """gpu/orc: dicts with row_ptr, col, val (finalized G), b, rec (records for
     `rows` in order, Nk[r] paths each).  b_extra_tol (per row, raw units) widens
     the b bound where part of b is computed at lower precision on purpose (the
     BF16 control variate).  atol_raw (per-path units; default ATOL_RAW) is the
     floor of fp32_path_atol for large patches; it scales with the square root
-    of the number of path weights in an entry.  Returns the flagged fraction."""
+    of the number of path weights in an entry.  rbf (RbfRows): records carry
+    no weights (RBF stencils); flagged paths' weights are rebuilt from their
+    exit side and coordinate.  Returns the flagged fraction."""
     Nk = np.asarray(Nk, dtype=np.int64)
     rows_index = np.repeat(np.arange(len(rows)), Nk)
     rg, ro = gpu["rec"], orc["rec"]
@@ -73,8 +76,12 @@ def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, at
         Go[r, k] = 0.0
     bg = np.asarray(gpu["b"])[rows] * Nk
     bo = np.asarray(orc["b"])[rows] * Nk
-    subtract_paths(Gg, bg, rg, flag, rows_index)
-    subtract_paths(Go, bo, ro, flag, rows_index)
+    if rbf is None:
+        subtract_paths(Gg, bg, rg, flag, rows_index)
+        subtract_paths(Go, bo, ro, flag, rows_index)
+    else:
+        subtract_paths_rbf(Gg, bg, rg, flag, rows_index, rows, rbf, side_g)
+        subtract_paths_rbf(Go, bo, ro, flag, rows_index, rows, rbf, ro["side"])
     err = np.abs(Gg - Go)
     if atol_raw is None:
         atol_g = ATOL_RAW
@@ -92,3 +99,71 @@ def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, at
     bbad = berr > RTOL * babs + atol_b + extra
     assert not bbad.any(), f"b mismatch rows {np.nonzero(bbad)[0][:5]}: {bg[bbad]} vs {bo[bbad]}"
     return frac
+
+
+class RbfRows:
+    """Per-path RBF weights rebuilt from a record (knot, exit side, s_line, Y)
+    with the oracle's FP64 cardinal functions, for removing flagged paths when
+    the records carry no weights (RBF stencils).  Stencils follow Eq. 13-17:
+    lattice patch of the knot, side line, segment extended by `ext` knots and
+    clipped to the closure of Omega."""
+
+    def __init__(self, orc, O, grid, c_abs):
+        self.orc, self.O = orc, O
+        self.m, self.ext = grid["m"], grid["ext"]
+        self.LX, self.LY = grid["Hx"] * grid["m"], grid["Hy"] * grid["m"]
+        self.dx = (grid["x1"] - grid["x0"]) / self.LX
+        self.dy = (grid["y1"] - grid["y0"]) / self.LY
+        self.x0, self.y0 = grid["x0"], grid["y0"]
+        self.c_abs = c_abs
+        self.index = {(int(round((x - self.x0) / self.dx)), int(round((y - self.y0) / self.dy))): q
+                      for q, (x, y) in enumerate(O.xy)}
+        self.cache = {}
+
+    def stencil(self, k, side):
+        i, j = (int(round((self.O.xy[k, 0] - self.x0) / self.dx)),
+                int(round((self.O.xy[k, 1] - self.y0) / self.dy)))
+        m = self.m
+        ilo, ihi = (i - m, i + m) if i % m == 0 else ((i // m) * m, (i // m) * m + m)
+        jlo, jhi = (j - m, j + m) if j % m == 0 else ((j // m) * m, (j // m) * m + m)
+        vertical = side in (0, 2)
+        line = {0: ihi, 1: jhi, 2: ilo, 3: jlo}[side]
+        lo, hi = (jlo, jhi) if vertical else (ilo, ihi)
+        lmax = self.LY if vertical else self.LX
+        a, b = max(lo - self.ext, 0), min(hi + self.ext, lmax)
+        cols = []
+        for tl in range(a, b + 1):
+            ij = (line, tl) if vertical else (tl, line)
+            cols.append(self.index.get(ij, -1))
+        return a, np.array(cols), vertical
+
+    def on_boundary(self, k, side):
+        i, j = (int(round((self.O.xy[k, 0] - self.x0) / self.dx)),
+                int(round((self.O.xy[k, 1] - self.y0) / self.dy)))
+        m = self.m
+        ilo, ihi = (i - m, i + m) if i % m == 0 else ((i // m) * m, (i // m) * m + m)
+        jlo, jhi = (j - m, j + m) if j % m == 0 else ((j // m) * m, (j // m) * m + m)
+        line = {0: ihi, 1: jhi, 2: ilo, 3: jlo}[side]
+        lmax = self.LY if side in (1, 3) else self.LX
+        return line == 0 or line == lmax
+
+    def weights(self, k, side, s_line, Y):
+        a, cols, vertical = self.stencil(k, side)
+        c_lat = self.c_abs / (self.dy if vertical else self.dx)
+        H = self.orc.rbf_cardinal(len(cols), c_lat, float(s_line) - a)
+        return cols, Y * H
+
+
+def subtract_paths_rbf(raw_G, raw_b, rec, sel, rows_index, rows, rbf, sides):
+    """Like subtract_paths for RBF records: weights rebuilt by `rbf`."""
+    for i in np.nonzero(sel)[0]:
+        r = rows_index[i]
+        k = rows[r]
+        side = int(sides[i])
+        raw_b[r] -= rec["b_contrib"][i]
+        if rbf.on_boundary(k, side):
+            continue
+        cols, w = rbf.weights(k, side, rec["s_line"][i], rec["Y"][i])
+        for c, wv in zip(cols, w):
+            if c >= 0:
+                raw_G[r, c] -= wv
