@@ -368,6 +368,8 @@ def main():
                     help="override paths per knot (small profiling cases; not a bench line)")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the CPU-oracle baseline and the end-to-end leg (profiling runs)")
+    ap.add_argument("--interp", default="linear", choices=["linear", "rbf"],
+                    help="stencil interpolation of the e1 pipeline (Sec. 2.1 RBF or linear)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiling runs count launches)")
     args = ap.parse_args()
@@ -485,7 +487,8 @@ def run_e1(args):
     torch.cuda.set_device(0)
     w = workload("e1")
     x = w.extra
-    kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"])
+    kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
+              rbf=args.interp == "rbf")
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []
@@ -507,6 +510,7 @@ def run_e1(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "knots": out["knots"], "eps": x["eps"],
                        "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
+                       "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
                        "note": "path-steps of the GM pass counted twice for the mixed run"},
             "pipeline": {
                 "phase1": {"ms": out["phase1"]["ms"], "path_steps": out["phase1"]["path_steps"],

@@ -64,11 +64,14 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
 
 def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | None = None,
         h0p: float | None = None, control_variate: bool = True, train_steps: int = 3000,
-        lr: float = 3e-3, solve_rtol: float = 1e-10) -> dict:
+        lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
+        rbf_shape: float = 0.0) -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
-    and step cap should be those of h0).  Returns the nodal solutions of
-    Phases I and III, the calibration (h_i, N_i, gap, var, rho^2), per-phase
-    wall times (CUDA-synchronized) and path-step counts."""
+    and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
+    instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
+    Returns the nodal solutions of Phases I and III, the calibration (h_i,
+    N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and
+    path-step counts."""
     import torch
     n0p = n0 if n0p is None else n0p
     h0p = h0 if h0p is None else h0p
@@ -76,7 +79,11 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     dev = P.dev
     n = P.n
     out = {"workload": w.name, "knots": n, "eps": eps, "n0": n0, "h0": h0, "n0p": n0p,
-           "h0p": h0p, "n_job": n_job, "control_variate": control_variate}
+           "h0p": h0p, "n_job": n_job, "control_variate": control_variate,
+           "interpolation": "rbf" if rbf else "linear"}
+    if rbf:
+        shape, terr = pdds.pdds_set_interpolation(P.ctx, pdds.PDDS_INTERP_RBF, rbf_shape)
+        out["rbf_shape"], out["rbf_table_err"] = shape, terr
 
     # Phase I: warm-up with Gobet-Menozzi exits
     pdds.pdds_set_scheme(P.ctx, pdds.PDDS_SCHEME_GM)
