@@ -63,7 +63,8 @@ class Grid(C.Structure):
 class Coeffs(C.Structure):
     _fields_ = [("id", C.c_int32), ("tab_nx", C.c_int32), ("tab_ny", C.c_int32),
                 ("pad_", C.c_int32), ("params", C.c_double * 8),
-                ("sigma_tab", C.c_void_p), ("c_tab", C.c_void_p), ("mlp", C.c_void_p)]
+                ("sigma_tab", C.c_void_p), ("c_tab", C.c_void_p), ("mlp", C.c_void_p),
+                ("cv_tab", C.c_void_p), ("cv_nx", C.c_int32), ("cv_ny", C.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side", "<i4"), ("flags", "<i4"),
@@ -160,6 +161,18 @@ class Problem:
         self.row_ptr = np.zeros(self.n + 1, dtype=np.int64)
         self.col = np.zeros(max(self.nnz, 1), dtype=np.int32)[: self.nnz]
         L.orc_geometry(C.byref(self.grid), _p(self.xy), _p(self.row_ptr), _p(self.col))
+
+    def set_cv_table(self, grad):
+        """Tabulated control variate: grad u0 at [ny][nx] nodes spanning Omega
+        (float32 [ny, nx, 2]), or None."""
+        if grad is None:
+            self.coef.cv_tab = None
+            self._cvt = None
+            return
+        self._cvt = np.ascontiguousarray(grad, dtype=np.float32)
+        assert self._cvt.ndim == 3 and self._cvt.shape[2] == 2
+        self.coef.cv_ny, self.coef.cv_nx = self._cvt.shape[:2]
+        self.coef.cv_tab = self._cvt.ctypes.data
 
     def set_mlp(self, theta):
         if theta is None:

@@ -256,6 +256,33 @@ static double e1_laplacian(double x, double y) {
   return (lap_sin + lap_tanh) / 3.0;
 }
 
+/* Tabulated grad u0 (Sec. 4.2's interpolatory look-up table of F / sigma):
+ * bilinear between the nodes of a [cv_ny][cv_nx] grid spanning Omega, the
+ * point clamped to the closure of Omega. */
+static void cv_table_grad(const orc_grid* g, const orc_coeffs* cf, double x, double y,
+                          double* gx, double* gy) {
+  const int nx = cf->cv_nx, ny = cf->cv_ny;
+  double fx = (x - g->x0) / (g->x1 - g->x0) * (nx - 1);
+  double fy = (y - g->y0) / (g->y1 - g->y0) * (ny - 1);
+  int i = (int)floor(fx), j = (int)floor(fy);
+  if (i < 0) i = 0;
+  if (i > nx - 2) i = nx - 2;
+  if (j < 0) j = 0;
+  if (j > ny - 2) j = ny - 2;
+  double tx = fx - i, ty = fy - j;
+  if (tx < 0) tx = 0;
+  if (tx > 1) tx = 1;
+  if (ty < 0) ty = 0;
+  if (ty > 1) ty = 1;
+  for (int q = 0; q < 2; ++q) {
+    const float* T = cf->cv_tab + q;
+    double v00 = T[2 * ((size_t)j * nx + i)], v10 = T[2 * ((size_t)j * nx + i + 1)];
+    double v01 = T[2 * ((size_t)(j + 1) * nx + i)], v11 = T[2 * ((size_t)(j + 1) * nx + i + 1)];
+    double v = (1 - tx) * (1 - ty) * v00 + tx * (1 - ty) * v10 + (1 - tx) * ty * v01 + tx * ty * v11;
+    if (q == 0) *gx = v; else *gy = v;
+  }
+}
+
 void orc_coeffs_eval(const orc_grid* g, const orc_coeffs* cf, double x, double y,
                      double* s, double* dx, double* dy, double* c, double* f) {
   const double pi = M_PI;
@@ -761,6 +788,10 @@ static void simulate(const sim_t* S, int k, int64_t p, int mode, path_out_t* em,
       double gx, gy;
       orc_mlp_grad_x(S->cf->mlp, X, Yp, &gx, &gy);
       xi -= Yw * s * (gx * dWx + gy * dWy);              /* F = sigma^T grad v */
+    } else if (S->cf->cv_tab) {                          /* F from the table  */
+      double gx, gy;
+      cv_table_grad(g, S->cf, X, Yp, &gx, &gy);
+      xi -= Yw * s * (gx * dWx + gy * dWy);
     }
     Sacc += c * h;                                       /* dY = c Y dt       */
     X += dxv * h + s * dWx;                              /* dX = d dt + s dW  */

@@ -36,6 +36,10 @@
  *                                  weights against the cardinal functions
  *   POISSON_E1 coefficients pinned: f against a finite-difference Laplacian
  *                                  of g = u of Eq. 43
+ *   tabulated control variate (cv_tab)
+ *                          pinned: a constant table equals the linear network
+ *                                  path for path; a table of grad u collapses
+ *                                  the score variance; unbiased
  *   orc_mlp_*              pinned: finite differences, closed-form special cases
  *   orc_lu_solve           pinned: residual and a library dense solve
  *   orc_bicgstab           pinned: agreement with orc_lu_solve and residual
@@ -95,6 +99,10 @@ typedef struct {
   const float* sigma_tab;/* [tab_ny][tab_nx] row-major, host                        */
   const float* c_tab;
   const double* mlp;     /* NULL = plain estimator; else ORC_MLP_NPARAM values      */
+  const float* cv_tab;   /* tabulated control variate (Sec. 4.2): grad u0 at the
+                            [cv_ny][cv_nx] nodes spanning Omega, (gx, gy) pairs,
+                            bilinear in between; used when mlp is NULL           */
+  int32_t cv_nx, cv_ny;
 } orc_coeffs;
 
 /* One record per simulated path (optional output of orc_assemble). */
