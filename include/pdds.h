@@ -118,7 +118,8 @@ typedef struct {
   int64_t truncated;        /* paths that reached the step cap                          */
   int64_t clamped;          /* interface exits clamped to the stencil ends              */
   int64_t units;            /* work units processed                                     */
-  int32_t device_error;     /* PDDS_OK or PDDS_ETIMEOUT from the last kernel            */
+  int32_t device_error;     /* PDDS_OK, PDDS_ETIMEOUT, or PDDS_EINVAL (an RBF exit found no
+                               table for its stencil: nothing deposited) from the last kernel */
   int32_t solve_iters;      /* iterations of the last pdds_solve                        */
   double solve_relres;      /* ||b - G u|| / ||b|| of the last pdds_solve               */
   float path_kernel_ms;     /* CUDA-event time of the last path kernel (timing on)     */

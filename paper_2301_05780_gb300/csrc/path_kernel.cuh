@@ -887,7 +887,8 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
         const float* cf = rbf_interval(D, vertical ? 1 : 0, L, r_s, tau);
         unsigned long long* acc = S.acc(r_st);
         double dsum = 0.0;
-        for (int j = lane; j < L; j += 32) {
+        if (cf == nullptr && lane == 0) atomicExch(&P.scratch->error, (int)PDDS_EINVAL);
+        for (int j = lane; cf != nullptr && j < L; j += 32) {
           const float w = r_Y * rbf_cardinal(cf, L, D.rbf_deg + 1, j, tau);
           const int tl = a + j;
           if (tl == 0 || tl == lmax) {

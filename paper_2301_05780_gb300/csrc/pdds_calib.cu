@@ -44,7 +44,7 @@ __device__ __forceinline__ double score(const PathRecordDev& r, const double* __
     const float* cf = rbf_interval(D, vertical ? 1 : 0, L, r.s_line - (float)a, tau);
     const int32_t* map = D.slot2csr + kd.slot_base + kd.off[side];
     double acc = 0.0;
-    for (int j = 0; j < L; ++j) {
+    for (int j = 0; cf != nullptr && j < L; ++j) {
       const int c = map[j];
       if (c < 0) continue;
       acc += (double)(r.Y * rbf_cardinal(cf, L, D.rbf_deg + 1, j, tau)) * u0[D.col[c]];

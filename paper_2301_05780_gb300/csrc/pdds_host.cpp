@@ -248,6 +248,7 @@ struct pdds_ctx {
   double* d_hknot = nullptr;  // owned copy of h_k, or nullptr
   double h_min = 0;           // smallest h_k (wait bound)
   // stencil interpolation: linear, or RBF with device tables
+  std::vector<int> stencil_len[2];  // distinct interface-stencil lengths per orientation
   int interp = PDDS_INTERP_LINEAR;
   double rbf_shape = 0;
   float* d_rbf_coef = nullptr;
@@ -639,6 +640,15 @@ pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx**
     return bail(e, "col upload");
   if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess) return bail(e, "event");
   if ((e = cudaEventCreate(&c->ev1)) != cudaSuccess) return bail(e, "event");
+  // Distinct interface-stencil lengths per orientation (0: lines along x, the
+  // N/S sides; 1: along y, the E/W sides), kept for the RBF tables.
+  for (const KnotDesc& d : G.kd)
+    for (int o = 0; o < 4; ++o) {
+      if ((d.dirbits >> o) & 1) continue;
+      const int L = d.b[o] - d.a[o] + 1;
+      std::vector<int>& v = c->stencil_len[(o == 0 || o == 2) ? 1 : 0];
+      if (std::find(v.begin(), v.end(), L) == v.end()) v.push_back(L);
+    }
   // Knot data on the host is only needed for coordinates from here on.
   c->geo.kd.clear();
   c->geo.kd.shrink_to_fit();
@@ -887,22 +897,15 @@ pdds_status pdds_set_interpolation(pdds_ctx* c, int32_t kind, double shape, doub
     return fail(c, PDDS_EINVAL, "set_interpolation: kind must be PDDS_INTERP_LINEAR or _RBF");
   if (!std::isfinite(shape)) return fail(c, PDDS_EINVAL, "set_interpolation: shape not finite");
   // stencil lengths per orientation (0: lines along x, sides N/S; 1: along y, E/W)
-  std::vector<int> len[2];
+  const std::vector<int>* len = c->stencil_len;
   int lmax_any = 0;
-  for (const KnotDesc& d : c->geo.kd)
-    for (int o = 0; o < 4; ++o) {
-      if ((d.dirbits >> o) & 1) continue;
-      const int L = d.b[o] - d.a[o] + 1;
-      const int orient = (o == 0 || o == 2) ? 1 : 0;
-      if (std::find(len[orient].begin(), len[orient].end(), L) == len[orient].end())
-        len[orient].push_back(L);
-      lmax_any = std::max(lmax_any, L);
-    }
+  for (int o = 0; o < 2; ++o)
+    for (int L : len[o]) lmax_any = std::max(lmax_any, L);
+  if (lmax_any < 2) return fail(c, PDDS_EINVAL, "set_interpolation: no interface stencils");
   const double sp[2] = {c->geo.dx, c->geo.dy};
   double cabs = shape;
   if (!(cabs > 0)) {
     // Sec. 5.1: c such that cond(Phi) of the longest stencil is 1e10
-    if (lmax_any < 2) return fail(c, PDDS_EINVAL, "set_interpolation: no interface stencils");
     cabs = pdds::rbf_shape_for_cond(lmax_any, 1e10) * std::min(sp[0], sp[1]);
   }
   const double c_lat[2] = {cabs / sp[0], cabs / sp[1]};

@@ -74,7 +74,7 @@ struct Scratch {
   unsigned long long truncated;
   unsigned long long clamped;
   unsigned long long units;
-  int32_t error;                  // 0 or PDDS_ETIMEOUT
+  int32_t error;                  // 0, PDDS_ETIMEOUT or PDDS_EINVAL (missing RBF table)
   int32_t pad_;
 };
 

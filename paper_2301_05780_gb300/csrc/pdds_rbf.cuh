@@ -10,14 +10,19 @@ namespace pdds {
 
 // Start of interval t's coefficients for an L-point stencil of orientation o
 // (0: line along x, 1: line along y), and tau for the coordinate s (lattice
-// spacings from the stencil's first knot, 0 <= s <= L - 1).
+// spacings from the stencil's first knot, 0 <= s <= L - 1).  nullptr when no
+// table exists for that length (the caller then deposits nothing and reports).
 __device__ __forceinline__ const float* rbf_interval(const ProbDesc& D, int o, int L, float s,
                                                      float& tau) {
+  tau = 0.f;
+  if (L < 2 || L > D.rbf_lmax) return nullptr;
+  const int64_t off = D.rbf_off[(int64_t)o * (D.rbf_lmax + 1) + L];
+  if (off < 0) return nullptr;
   int t = (int)floorf(s);
   t = max(0, min(t, L - 2));
   tau = fmaf(2.0f, s - (float)t, -1.0f);
   const int P1 = D.rbf_deg + 1;
-  return D.rbf_coef + D.rbf_off[(int64_t)o * (D.rbf_lmax + 1) + L] + (int64_t)t * P1 * L;
+  return D.rbf_coef + off + (int64_t)t * P1 * L;
 }
 
 // H_j(tau) by Clenshaw's recurrence.
