@@ -65,10 +65,13 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
 def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | None = None,
         h0p: float | None = None, control_variate: bool = True, train_steps: int = 3000,
         lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
-        rbf_shape: float = 0.0) -> dict:
+        rbf_shape: float = 0.0, cv_kind: str = "table") -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
     and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
     instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
+    cv_kind: "table" tabulates grad v_theta on a grid of half the knot spacing
+    (the paper's look-up table of Sec. 4.2, four reads per step) or "network"
+    evaluates v_theta in the path (two 64 x 64 products per step).
     Returns the nodal solutions of Phases I and III, the calibration (h_i,
     N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and
     path-step counts."""
@@ -103,8 +106,23 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     if control_variate:
         xy = pdds.pdds_knot_coords(P.ctx)
         (theta, hist), tfit = _sync_ms(lambda: fit_network(xy, u0, w.grid, train_steps, lr, dev))
-        pdds.pdds_set_control_variate(P.ctx, theta)
-        out["fit"] = {"ms": tfit, "steps": train_steps, "final_loss": float(hist[-1])}
+        if cv_kind == "network":
+            pdds.pdds_set_control_variate(P.ctx, theta)
+            ttab = 0.0
+        else:
+            def tabulate():
+                nx = 2 * w.grid["Hx"] * w.grid["m"] + 1
+                ny = 2 * w.grid["Hy"] * w.grid["m"] + 1
+                gx = torch.linspace(w.grid["x0"], w.grid["x1"], nx, dtype=torch.float32,
+                                    device=dev)
+                gy = torch.linspace(w.grid["y0"], w.grid["y1"], ny, dtype=torch.float32,
+                                    device=dev)
+                pts = torch.stack(torch.meshgrid(gx, gy, indexing="xy"), dim=-1).reshape(-1, 2)
+                _, grad = pdds.pdds_mlp_eval(theta, pts.contiguous())
+                pdds.pdds_set_control_variate_grid(P.ctx, grad.reshape(ny, nx, 2))
+            _, ttab = _sync_ms(tabulate)
+        out["fit"] = {"ms": tfit + ttab, "steps": train_steps, "final_loss": float(hist[-1]),
+                      "cv_kind": cv_kind}
 
     # Phase II: mixed GM/EM calibration and Eq. 40-41
     mom = torch.empty(n, pdds.CAL_NMOM, dtype=torch.float64, device=dev)

@@ -385,6 +385,25 @@ __device__ __forceinline__ const ProbDesc& prob_desc(const KParams& P, int i) {
   return P.nprob == 1 ? P.prob0 : P.probs[i];
 }
 
+// Tabulated control variate (Sec. 4.2): grad u0 at the [cv_ny][cv_nx] nodes
+// spanning Omega as (gx, gy) pairs, bilinear in between (read through L1/L2;
+// neighbouring lanes follow paths of the same knot, so their reads overlap).
+__device__ __forceinline__ void cv_table_grad(const ProbDesc& D, float x, float y, float& gx,
+                                              float& gy) {
+  const float fx = (x - D.x0) * D.cv_inv_dx, fy = (y - D.y0) * D.cv_inv_dy;
+  const int i = min(max((int)floorf(fx), 0), D.cv_nx - 2);
+  const int j = min(max((int)floorf(fy), 0), D.cv_ny - 2);
+  const float tx = fminf(fmaxf(fx - (float)i, 0.f), 1.f);
+  const float ty = fminf(fmaxf(fy - (float)j, 0.f), 1.f);
+  const float2* r0 = reinterpret_cast<const float2*>(D.cv_tab) + (int64_t)j * D.cv_nx + i;
+  const float2* r1 = r0 + D.cv_nx;
+  const float2 a = __ldg(r0), b = __ldg(r0 + 1), c = __ldg(r1), d = __ldg(r1 + 1);
+  const float x0 = fmaf(tx, b.x - a.x, a.x), x1 = fmaf(tx, d.x - c.x, c.x);
+  const float y0 = fmaf(tx, b.y - a.y, a.y), y1 = fmaf(tx, d.y - c.y, c.y);
+  gx = fmaf(ty, x1 - x0, x0);
+  gy = fmaf(ty, y1 - y0, y0);
+}
+
 // ------------------------------------------------------------ unit loading
 __device__ int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t v) {
   int64_t lo = 0, hi = n;  // first index with a[i] > v
@@ -555,26 +574,27 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 // ------------------------------------------------------------- the kernel
-// Plain variants: up to 1024 threads (64 registers).  Control-variate variants
-// hold the MMA fragments of the in-path network: at most 256 threads and two
-// CTAs per SM, i.e. up to 128 registers.  EXT: per-knot steps and the
+// CV: 0 no control variate, 1 the in-path network, 2 the tabulated gradient.
+// Plain and table variants: up to 1024 threads (64 registers).  Network
+// variants hold the MMA fragments of the in-path network: at most 256 threads
+// and two CTAs per SM, i.e. up to 128 registers.  EXT: per-knot steps and the
 // Gobet-Menozzi shift (P.gm).
-template <int COEF, bool RECORD, bool CV, bool EXT>
-__global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
+template <int COEF, bool RECORD, int CV, bool EXT>
+__global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
     path_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   // Control variate: the network is staged once per CTA at the start of the
-  // dynamic shared memory (CV variants only); the unit ring follows it.
+  // dynamic shared memory (network variants only); the unit ring follows it.
   MlpSmem* mlp_s = reinterpret_cast<MlpSmem*>(smem_raw);
-  if constexpr (CV) {
+  if constexpr (CV == 1) {
     const int4* src = reinterpret_cast<const int4*>(P.mlp);
     int4* dst = reinterpret_cast<int4*>(mlp_s);
     for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
   }
   Smem S;
-  S.base = smem_raw + (CV ? kMlpSmemBytes : 0);
+  S.base = smem_raw + (CV == 1 ? kMlpSmemBytes : 0);
   S.stage_bytes = P.stage_bytes;
   S.acc_bytes = ((P.max_slots * 8) + 127) / 128 * 128;
   S.tile_bytes = ((P.tile_w * P.tile_h * 4) + 127) / 128 * 128;
@@ -686,7 +706,7 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
     const int64_t kmax = EXT ? kmax_l : P.kmax;
     bool exited = false, trunc = false;
     for (;;) {
-      if constexpr (CV) {
+      if constexpr (CV == 1) {
         // Same step as below, but the warp stays converged for the tensor-core
         // evaluation of grad v_theta at every lane's position; only lanes that
         // are stepping use it: dxi = -Y sigma grad v . dW (Eq. 37).
@@ -738,8 +758,9 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
             float s, ddx, ddy, c, f;
             coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
                          s, ddx, ddy, c, f);
+            float Yw = 1.0f;
             if constexpr (has_c<COEF>()) {
-              const float Yw = __expf(Sx);
+              Yw = __expf(Sx);
               Z = fmaf(-f * Yw, h, Z);  // dZ = -f Y dt
               Sx = fmaf(c, h, Sx);      // dY = c Y dt, Y = exp(S)
             } else if constexpr (has_f<COEF>()) {
@@ -747,6 +768,12 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
             }
             // dX = d dt + s dW with dW = sqrt(h) z: s sqrt(h) once, then two FMAs
             const float ssh = s * sqh;
+            if constexpr (CV == 2) {
+              // dxi = -Y s grad u0 . dW with grad u0 from the table (Eq. 37, Sec. 4.2)
+              float gx, gy;
+              cv_table_grad(prob_desc(P, H.prob), xk + X, yk + Y, gx, gy);
+              XI = fmaf(-Yw * ssh, fmaf(gx, z[2 * half], gy * z[2 * half + 1]), XI);
+            }
             if constexpr (has_drift<COEF>()) {
               X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
               Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
@@ -807,7 +834,7 @@ __global__ void __launch_bounds__(CV ? 256 : 1024, CV ? 2 : 1)
       }
       if constexpr (has_c<COEF>()) Yk = __expf(Sx);
       bc = (double)Z;
-      if constexpr (CV) bc += (double)XI;
+      if constexpr (CV != 0) bc += (double)XI;
       const bool vertical = (side == 0 || side == 2);
       flags = trunc ? 1 : 0;
       if ((kd.dirbits >> side) & 1) {

@@ -241,7 +241,9 @@ struct pdds_ctx {
   cudaStream_t cap_stream = nullptr;
   // control variate (staged network image) and whether it is on
   void* d_mlp = nullptr;
-  bool cv_on = false;
+  int cv_mode = 0;               // 0 none, 1 in-path network, 2 tabulated gradient
+  float* d_cvtab = nullptr;      // [cv_ny][cv_nx][2] grad u0 (mode 2), owned
+  int cv_nx = 0, cv_ny = 0;
   bool unit_domain_all = false;  // set by a batched launch: all its domains in [-1,1]^2
   // exit scheme and per-knot steps (extended-exit kernels)
   int scheme = PDDS_SCHEME_EM;
@@ -296,7 +298,7 @@ void free_ctx(pdds_ctx* c) {
   cudaFree(c->d_mlp);
   cudaFree(c->d_hknot); cudaFree(c->cal_rec); cudaFree(c->cal_val); cudaFree(c->cal_b);
   cudaFree(c->cal_rp); cudaFree(c->cal_col);
-  cudaFree(c->d_rbf_coef); cudaFree(c->d_rbf_off);
+  cudaFree(c->d_rbf_coef); cudaFree(c->d_rbf_off); cudaFree(c->d_cvtab);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -344,6 +346,13 @@ ProbDesc make_prob(const pdds_ctx* c, int tag) {
   D.tag = tag;
   D.sigma_max = (float)(c->s_max * (1.0 + 1e-6));  // bilinear lookups may round up 1 ulp
   D.h_per_knot = c->d_hknot;
+  if (c->cv_mode == 2) {
+    D.cv_tab = c->d_cvtab;
+    D.cv_nx = c->cv_nx;
+    D.cv_ny = c->cv_ny;
+    D.cv_inv_dx = (float)((c->cv_nx - 1) / (c->grid.x1 - c->grid.x0));
+    D.cv_inv_dy = (float)((c->cv_ny - 1) / (c->grid.y1 - c->grid.y0));
+  }
   if (c->interp == PDDS_INTERP_RBF) {
     D.rbf_coef = c->d_rbf_coef;
     D.rbf_off = c->d_rbf_off;
@@ -403,8 +412,8 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   const double kmax_eff = ext && c->d_hknot && c->h_min < dt ? (double)kmax * dt / c->h_min
                                                              : (double)kmax;
   kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * kmax_eff);
-  const bool cv = nprob == 1 && c->cv_on;
-  kp.mlp = cv ? c->d_mlp : nullptr;
+  const int cv = nprob == 1 ? c->cv_mode : 0;
+  kp.mlp = cv == 1 ? c->d_mlp : nullptr;
   {
     // all problems of the launch inside [-1, 1]^2 (problem 0 here, the batch
     // caller checks the rest through c->unit_domain_all)
@@ -413,12 +422,12 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
                     std::fabs(g.y1) <= 1;
     kp.unit_domain = (nprob == 1 ? u0 : c->unit_domain_all) ? 1 : 0;
   }
-  // the control-variate step is ~10x heavier: wait bounds scale with it
-  if (cv && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
-  // CV kernels keep the staged network at the start of dynamic shared memory
-  const size_t smem = 2 * sbytes + (cv ? round_up(pdds::mlp_image_bytes(), 128) : 0);
+  // the network step is ~10x heavier: wait bounds scale with it
+  if (cv == 1 && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
+  // network kernels keep the staged network at the start of dynamic shared memory
+  const size_t smem = 2 * sbytes + (cv == 1 ? round_up(pdds::mlp_image_bytes(), 128) : 0);
   CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, ext, smem));
-  const int block = cv ? std::min(c->block, 256) : c->block;  // CV kernels: <= 256 threads
+  const int block = cv == 1 ? std::min(c->block, 256) : c->block;  // network: <= 256 threads
   int per_sm = c->ctas_per_sm;
   if (per_sm <= 0) {
     CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, ext, block, smem, &per_sm));
@@ -739,7 +748,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   static std::map<Key, Shape> cache;
   // xk: the extended-exit kernel (GM scheme or per-knot steps) is a different kernel
   const int xk = (c->scheme == PDDS_SCHEME_GM ? 1 : 0) + (c->d_hknot ? 2 : 0);
-  const Key key{c->device, c->coef_id, c->cv_on ? 1 : 0, xk, c->grid.Hx, c->grid.Hy, c->grid.m,
+  const Key key{c->device, c->coef_id, c->cv_mode, xk, c->grid.Hx, c->grid.Hy, c->grid.m,
                 c->grid.ext, n_paths};
   {
     std::lock_guard<std::mutex> lock(mu);
@@ -785,7 +794,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   for (int bl : blocks)
     for (int un : units)
       for (int ba : batches)
-        if (!(c->cv_on && bl > 256)) shapes.push_back(Shape{bl, un, ba});
+        if (!(c->cv_mode == 1 && bl > 256)) shapes.push_back(Shape{bl, un, ba});
   std::vector<float> ms(shapes.size(), 1e30f);
   for (int round = 0; round < 2 && st == PDDS_OK; ++round)
     for (size_t i = 0; i < shapes.size() && st == PDDS_OK; ++i) {
@@ -832,7 +841,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
 pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_control_variate: NULL context");
   if (!theta) {
-    c->cv_on = false;
+    c->cv_mode = 0;
     return PDDS_OK;
   }
   if (!pdds::path_kernel_has_cv(c->coef_id))
@@ -841,7 +850,31 @@ pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
   if (!c->d_mlp) CK(c, cudaMalloc(&c->d_mlp, pdds::mlp_image_bytes()));
   CK(c, pdds::mlp_stage(theta, c->d_mlp, nullptr));
   CK(c, cudaDeviceSynchronize());
-  c->cv_on = true;
+  c->cv_mode = 1;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_control_variate_grid(pdds_ctx* c, const float* grad_xy, int32_t nx,
+                                          int32_t ny) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_control_variate_grid: NULL context");
+  if (!grad_xy) {
+    c->cv_mode = 0;
+    return PDDS_OK;
+  }
+  if (nx < 2 || ny < 2 || (int64_t)nx * ny > ((int64_t)1 << 28))
+    return fail(c, PDDS_EINVAL, "set_control_variate_grid: need 2 <= nx, ny and nx*ny <= 2^28");
+  (void)cudaGetLastError();
+  const size_t count = (size_t)nx * ny * 2;
+  if (c->cv_nx * c->cv_ny != nx * ny) {
+    CK(c, cudaFree(c->d_cvtab));
+    c->d_cvtab = nullptr;
+    if (dalloc(&c->d_cvtab, count) != cudaSuccess)
+      return fail(c, PDDS_ENOMEM, "set_control_variate_grid: table allocation failed");
+  }
+  CK(c, cudaMemcpy(c->d_cvtab, grad_xy, count * 4, cudaMemcpyDefault));
+  c->cv_nx = nx;
+  c->cv_ny = ny;
+  c->cv_mode = 2;
   return PDDS_OK;
 }
 
@@ -1128,7 +1161,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same coefficient set");
     if (c->device != c0->device)
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same device");
-    if (c->cv_on)
+    if (c->cv_mode)
       return fail(c0, PDDS_EINVAL, "assemble_batch: control variates are not supported in batches");
     if (c->scheme != PDDS_SCHEME_EM || c->d_hknot || c->interp != PDDS_INTERP_LINEAR)
       return fail(c0, PDDS_EINVAL,
@@ -1193,7 +1226,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
       if (c0->coef_id == PDDS_COEF_TABLE) x += 2 * round_up((size_t)tw * th * 4, 128);
       return round_up(x, 128);
     }();
-    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, false, false, 2 * sb));
+    CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, 0, false, 2 * sb));
     // Capture on a private non-blocking stream (the legacy default stream
     // cannot be captured); the instantiated graph is launched on the caller's.
     if (!c0->cap_stream) CK(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));

@@ -63,6 +63,10 @@ struct ProbDesc {
   const float* rbf_coef;          // RBF stencils (extended kernels), or nullptr: linear
   const int64_t* rbf_off;         // [2][rbf_lmax + 1] table offset per (orientation, length)
   int32_t rbf_lmax;
+  int32_t cv_nx;                  // tabulated control variate: nodes per row, or 0
+  const float* cv_tab;            // [cv_ny][cv_nx][2] grad u0 spanning Omega, or nullptr
+  int32_t cv_ny;
+  float cv_inv_dx, cv_inv_dy;     // table nodes per unit length
   int32_t pad1_;
 };
 
@@ -111,12 +115,13 @@ struct KParams {
 };
 
 // Launchers implemented in the .cu files (host-callable).
-// `ext` selects the extended-exit variants (per-knot steps, Gobet-Menozzi shift).
-cudaError_t launch_path_kernel(int coef_id, bool records, bool cv, bool ext, const KParams& kp,
+// `cv`: 0 none, 1 in-path network, 2 tabulated gradient; `ext` selects the
+// extended-exit variants (per-knot steps, Gobet-Menozzi shift, RBF stencils).
+cudaError_t launch_path_kernel(int coef_id, bool records, int cv, bool ext, const KParams& kp,
                                int grid, int block, size_t smem, cudaStream_t stream);
-cudaError_t path_kernel_occupancy(int coef_id, bool records, bool cv, bool ext, int block,
+cudaError_t path_kernel_occupancy(int coef_id, bool records, int cv, bool ext, int block,
                                   size_t smem, int* ctas_per_sm);
-cudaError_t set_path_kernel_smem(int coef_id, bool records, bool cv, bool ext, size_t smem);
+cudaError_t set_path_kernel_smem(int coef_id, bool records, int cv, bool ext, size_t smem);
 bool path_kernel_has_cv(int coef_id);
 // Control-variate network (pdds_mlp.cu): FP32 theta -> staged image.
 size_t mlp_image_bytes();

@@ -66,24 +66,33 @@ __global__ void finalize_kernel(const int32_t* __restrict__ row_ptr, const int32
 
 }  // namespace
 
-// Kernel variants, one translation unit each (pdds_path_em.cu, ...):
-// plain / control variate, each with and without the extended exit (per-knot
-// steps and the Gobet-Menozzi shift).  nullptr: no such variant.
+// Kernel variants, one translation unit each (pdds_path_em.cu, ...): no
+// control variate / in-path network / tabulated gradient, each with and
+// without the extended exit (per-knot steps, Gobet-Menozzi shift, RBF
+// stencils).  nullptr: no such variant.
 void* path_kernel_em(int coef, bool rec);
 void* path_kernel_cv(int coef, bool rec);
+void* path_kernel_cvt(int coef, bool rec);
 void* path_kernel_ext(int coef, bool rec);
 void* path_kernel_ext_cv(int coef, bool rec);
+void* path_kernel_ext_cvt(int coef, bool rec);
 
 namespace {
-void* pick(int coef, bool rec, bool cv, bool ext) {
-  if (ext) return cv ? path_kernel_ext_cv(coef, rec) : path_kernel_ext(coef, rec);
-  return cv ? path_kernel_cv(coef, rec) : path_kernel_em(coef, rec);
+void* pick(int coef, bool rec, int cv, bool ext) {
+  if (ext) {
+    if (cv == 1) return path_kernel_ext_cv(coef, rec);
+    if (cv == 2) return path_kernel_ext_cvt(coef, rec);
+    return path_kernel_ext(coef, rec);
+  }
+  if (cv == 1) return path_kernel_cv(coef, rec);
+  if (cv == 2) return path_kernel_cvt(coef, rec);
+  return path_kernel_em(coef, rec);
 }
 }  // namespace
 
-bool path_kernel_has_cv(int coef) { return pick(coef, false, true, false) != nullptr; }
+bool path_kernel_has_cv(int coef) { return pick(coef, false, 1, false) != nullptr; }
 
-cudaError_t launch_path_kernel(int coef, bool rec, bool cv, bool ext, const KParams& kp, int grid,
+cudaError_t launch_path_kernel(int coef, bool rec, int cv, bool ext, const KParams& kp, int grid,
                                int block, size_t smem, cudaStream_t stream) {
   void* fn = pick(coef, rec, cv, ext);
   if (!fn) return cudaErrorInvalidValue;
@@ -91,14 +100,14 @@ cudaError_t launch_path_kernel(int coef, bool rec, bool cv, bool ext, const KPar
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
-cudaError_t path_kernel_occupancy(int coef, bool rec, bool cv, bool ext, int block, size_t smem,
+cudaError_t path_kernel_occupancy(int coef, bool rec, int cv, bool ext, int block, size_t smem,
                                   int* ctas) {
   void* fn = pick(coef, rec, cv, ext);
   if (!fn) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
 }
 
-cudaError_t set_path_kernel_smem(int coef, bool rec, bool cv, bool ext, size_t smem) {
+cudaError_t set_path_kernel_smem(int coef, bool rec, int cv, bool ext, size_t smem) {
   void* fn = pick(coef, rec, cv, ext);
   if (!fn) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

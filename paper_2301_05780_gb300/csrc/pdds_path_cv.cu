@@ -1,12 +1,12 @@
-// Control-variate path-kernel variants (naive EM exit): the analytic sets
-// used with a learned v_theta and the constant test set.
+// Control-variate path-kernel variants with the in-path network (naive EM
+// exit): the analytic sets used with a learned v_theta and the constant set.
 #include "path_kernel.cuh"
 
 namespace pdds {
 namespace {
 template <int COEF, bool REC>
 void* ptr() {
-  return reinterpret_cast<void*>(&path_kernel<COEF, REC, true, false>);
+  return reinterpret_cast<void*>(&path_kernel<COEF, REC, 1, false>);
 }
 }  // namespace
 

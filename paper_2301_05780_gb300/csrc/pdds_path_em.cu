@@ -5,7 +5,7 @@ namespace pdds {
 namespace {
 template <int COEF, bool REC>
 void* ptr() {
-  return reinterpret_cast<void*>(&path_kernel<COEF, REC, false, false>);
+  return reinterpret_cast<void*>(&path_kernel<COEF, REC, 0, false>);
 }
 }  // namespace
 

@@ -1,12 +1,12 @@
-// Extended-exit path-kernel variants: per-knot steps h_k and the
-// Gobet-Menozzi shift of the patch sides (Sec. 2.3).
+// Extended-exit path-kernel variants: per-knot steps h_k, the
+// Gobet-Menozzi shift of the patch sides (Sec. 2.3) and RBF stencils.
 #include "path_kernel.cuh"
 
 namespace pdds {
 namespace {
 template <int COEF, bool REC>
 void* ptr() {
-  return reinterpret_cast<void*>(&path_kernel<COEF, REC, false, true>);
+  return reinterpret_cast<void*>(&path_kernel<COEF, REC, 0, true>);
 }
 }  // namespace
 

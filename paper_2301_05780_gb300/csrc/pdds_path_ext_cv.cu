@@ -1,12 +1,12 @@
-// Extended-exit control-variate path-kernel variants (production runs of
-// the calibrated pipeline: per-knot h_k, Gobet-Menozzi shift, xi of Eq. 37).
+// Extended-exit path-kernel variants with the in-path network (per-knot h_k,
+// Gobet-Menozzi shift, RBF stencils, xi of Eq. 37).
 #include "path_kernel.cuh"
 
 namespace pdds {
 namespace {
 template <int COEF, bool REC>
 void* ptr() {
-  return reinterpret_cast<void*>(&path_kernel<COEF, REC, true, true>);
+  return reinterpret_cast<void*>(&path_kernel<COEF, REC, 1, true>);
 }
 }  // namespace
 

@@ -95,6 +95,7 @@ _SIGS = {
     "pdds_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
     "pdds_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "pdds_set_control_variate": (C.c_int, [_P, _P]),
+    "pdds_set_control_variate_grid": (C.c_int, [_P, _P, C.c_int32, C.c_int32]),
     "pdds_assemble_solve_host": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_double,
                                            C.c_int32, _P, _P, _P, _P, _P, _P]),
     "pdds_stats": (C.c_int, [_P, _P]),
@@ -361,6 +362,16 @@ def pdds_mlp_eval(theta, xy, stream=None):
 
 def pdds_set_control_variate(ctx, theta):
     _check(lib().pdds_set_control_variate(ctx, _dptr(theta)), ctx)
+
+
+def pdds_set_control_variate_grid(ctx, grad):
+    """Tabulated control variate: grad u0 at [ny, nx] nodes spanning Omega
+    (float32 tensor [ny, nx, 2], device or pinned host), or None to detach."""
+    if grad is None:
+        _check(lib().pdds_set_control_variate_grid(ctx, None, 0, 0), ctx)
+        return
+    ny, nx = int(grad.shape[0]), int(grad.shape[1])
+    _check(lib().pdds_set_control_variate_grid(ctx, _dptr(grad.contiguous()), nx, ny), ctx)
 
 
 def pdds_assemble_solve_host(ctx, n_paths, dt, seed, rtol, maxit, row_ptr, col, val, b, u,

@@ -54,15 +54,22 @@ def run_pair(orc, w, cond, scheme=pdds.PDDS_SCHEME_EM, rows=None):
     return g, o, O, c_abs
 
 
+def _longest_interface_stencil(orc, w):
+    O = orc.Problem(w.grid, w.coef_id, w.params)
+    rbf = parity.RbfRows(orc, O, w.grid, 1.0)
+    return max(len(rbf.stencil(k, side)[1]) for k in range(O.n) for side in range(4)
+               if not rbf.on_boundary(k, side))
+
+
 def test_auto_shape_matches_the_condition_rule(orc):
-    """rbf_shape <= 0 picks c with cond(Phi) = 1e10 on the longest stencil
-    (Sec. 5.1); the library's power/inverse iteration and the oracle's Jacobi
-    eigenvalues agree on that c."""
+    """rbf_shape <= 0 picks c with cond(Phi) = 1e10 on the longest interface
+    stencil (Sec. 5.1); the library's power/inverse iteration and the
+    oracle's Jacobi eigenvalues agree on that c."""
     w = _small(10)
     P = pdds.Problem(w)
     used, terr = pdds.pdds_set_interpolation(P.ctx, pdds.PDDS_INTERP_RBF, 0.0)
     spacing = 1.0 / (w.grid["Hx"] * w.grid["m"])
-    ref = orc.rbf_shape_for_cond(_longest_stencil(w.grid), 1e10) * spacing
+    ref = orc.rbf_shape_for_cond(_longest_interface_stencil(orc, w), 1e10) * spacing
     assert used == pytest.approx(ref, rel=1e-4)
     assert terr < 1e-5
     pdds.pdds_set_interpolation(P.ctx, pdds.PDDS_INTERP_LINEAR)
