@@ -155,11 +155,13 @@ pdds_status pdds_set_launch(pdds_ctx* ctx, int32_t block, int32_t ctas_per_sm,
                             int32_t unit_paths, int32_t exit_batch);
 pdds_status pdds_get_launch(const pdds_ctx* ctx, int32_t* block, int32_t* ctas_per_sm,
                             int32_t* unit_paths, int32_t* exit_batch);
-/* Autotuner: times short assemblies of a sample of the knots (every 8th, at
- * the full per-knot budget n_paths, time step dt) for every combination of
- * block in {128, 256, 512}, unit_paths in {1024, 4096, 16384} and exit_batch
- * in {2, 4, 8}, twice each; the four fastest are then timed twice on the whole
- * problem (every knot at n_paths) and the fastest of those is kept.  The launch shape
+/* Autotuner: times short assemblies of a sample of the knots (every k-th,
+ * k >= 8 chosen so that the sample has at most 2e8 paths, each at the full
+ * per-knot budget n_paths, time step dt) for every combination of block in
+ * {64, 128, 256, 512}, unit_paths in {256, 1024, 4096, 16384} and exit_batch in
+ * {2, 4, 8, 16}; the twelve fastest are timed again; the three fastest of those
+ * are timed twice on the whole problem (on every k2-th knot when it has more
+ * than 1e9 paths) and the fastest is kept.  The launch shape
  * only reorders floating-point additions, never the estimator.  Results are
  * cached for the process per (device, coefficient set, control variate on/off,
  * grid, n_paths); a cached shape is applied without timing.  Allocates and

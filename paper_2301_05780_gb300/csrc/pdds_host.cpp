@@ -764,62 +764,71 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = c->geo.n, nnz = c->geo.nnz;
-  // Sample every 8th knot (at least one) at the full budget; others get none.
-  std::vector<int64_t> Nh(n, 0);
-  for (int64_t k = 0; k < n; k += 8) Nh[k] = n_paths;
-  int64_t* dN = nullptr;
+  // Stage 1 sample: every k-th knot at the full budget (others get none), k >= 8
+  // and large enough that the sample has at most 2e8 paths; the finalists run on
+  // the whole problem, or on every k2-th knot when it has more than 1e9 paths.
+  const int64_t total = n * n_paths;
+  const int64_t k1 = std::max<int64_t>(8, (total + 199999999) / 200000000);
+  const int64_t k2 = std::max<int64_t>(1, (total + 999999999) / 1000000000);
+  std::vector<int64_t> Nh(n, 0), Nf(n, 0);
+  for (int64_t k = 0; k < n; k += k1) Nh[k] = n_paths;
+  for (int64_t k = 0; k < n; k += k2) Nf[k] = n_paths;
+  int64_t *dN = nullptr, *dF = nullptr;
   int32_t *rp = nullptr, *col = nullptr;
   double *val = nullptr, *b = nullptr;
-  auto cleanup = [&] { cudaFree(dN); cudaFree(rp); cudaFree(col); cudaFree(val); cudaFree(b); };
-  if (dalloc(&dN, n) || dalloc(&rp, n + 1) || dalloc(&col, nnz) || dalloc(&val, nnz) ||
-      dalloc(&b, n)) {
+  auto cleanup = [&] {
+    cudaFree(dN); cudaFree(dF); cudaFree(rp); cudaFree(col); cudaFree(val); cudaFree(b);
+  };
+  if (dalloc(&dN, n) || dalloc(&dF, n) || dalloc(&rp, n + 1) || dalloc(&col, nnz) ||
+      dalloc(&val, nnz) || dalloc(&b, n)) {
     cleanup();
     return fail(c, PDDS_ENOMEM, "autotune: scratch allocation failed");
   }
   pdds_csr G{n, nnz, rp, col, val};
   pdds_status st = PDDS_OK;
-  if (cudaMemcpy(dN, Nh.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpy(dN, Nh.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dF, Nf.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
     st = fail(c, PDDS_ECUDA, "autotune: upload failed");
   const bool timing = c->timing;
-  const int blocks[] = {128, 256, 512};
-  const int units[] = {1024, 4096, 16384};
-  const int batches[] = {2, 4, 8};
+  // Short paths (few steps per exit) favour small CTAs and units: all warps of a
+  // CTA refill from its two staged units, so large CTAs contend on them.
+  const int blocks[] = {64, 128, 256, 512};
+  const int units[] = {256, 1024, 4096, 16384};
+  const int batches[] = {2, 4, 8, 16};
   Shape best{c->block, (int)c->unit_paths, c->exit_batch};
   c->timing = true;
   c->ctas_per_sm = 0;
-  // two interleaved rounds; a shape's time is its faster round (a single
-  // timing of a few milliseconds is noisy at the 2-3 % level that separates
-  // the best shapes)
   std::vector<Shape> shapes;
   for (int bl : blocks)
     for (int un : units)
       for (int ba : batches)
         if (!(c->cv_mode == 1 && bl > 256)) shapes.push_back(Shape{bl, un, ba});
+  auto time_shape = [&](const Shape& sh, const int64_t* N, int64_t Nu, float& ms) {
+    c->block = sh.block;
+    c->unit_paths = sh.unit;
+    c->exit_batch = sh.batch;
+    st = assemble_impl(c, N, Nu, dt, seed, &G, b, nullptr, s);
+    if (st == PDDS_OK) ms = std::min(ms, c->st.path_kernel_ms);
+  };
+  // round 1: every shape once on the sample; round 2: the best twelve again
+  // (a few-millisecond timing is noisy at the 2-3 % that separates the best)
   std::vector<float> ms(shapes.size(), 1e30f);
-  for (int round = 0; round < 2 && st == PDDS_OK; ++round)
-    for (size_t i = 0; i < shapes.size() && st == PDDS_OK; ++i) {
-      c->block = shapes[i].block;
-      c->unit_paths = shapes[i].unit;
-      c->exit_batch = shapes[i].batch;
-      st = assemble_impl(c, dN, 0, dt, seed, &G, b, nullptr, s);
-      if (st == PDDS_OK) ms[i] = std::min(ms[i], c->st.path_kernel_ms);
-    }
-  // The sample's tail (few units left, lanes idle) weighs more than in the
-  // full problem, so the four best shapes of the sample are timed again, twice
-  // each, on the whole problem (every knot at n_paths), and the fastest wins.
+  for (size_t i = 0; i < shapes.size() && st == PDDS_OK; ++i) time_shape(shapes[i], dN, 0, ms[i]);
   std::vector<size_t> order(shapes.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b2) { return ms[a] < ms[b2]; });
-  const size_t finalists = std::min<size_t>(4, order.size());
+  auto by_ms = [&](size_t a, size_t b2) { return ms[a] < ms[b2]; };
+  std::stable_sort(order.begin(), order.end(), by_ms);
+  for (size_t f = 0; f < std::min<size_t>(12, order.size()) && st == PDDS_OK; ++f)
+    time_shape(shapes[order[f]], dN, 0, ms[order[f]]);
+  std::stable_sort(order.begin(), order.end(), by_ms);
+  // The sample's tail (few units left, lanes idle) weighs more than in the
+  // full problem, so the three best are timed twice more on the large sample.
+  const size_t finalists = std::min<size_t>(3, order.size());
   std::vector<float> full(finalists, 1e30f);
   for (int round = 0; round < 2 && st == PDDS_OK; ++round)
     for (size_t f = 0; f < finalists && st == PDDS_OK; ++f) {
-      const Shape& sh = shapes[order[f]];
-      c->block = sh.block;
-      c->unit_paths = sh.unit;
-      c->exit_batch = sh.batch;
-      st = assemble_impl(c, nullptr, n_paths, dt, seed, &G, b, nullptr, s);
-      if (st == PDDS_OK) full[f] = std::min(full[f], c->st.path_kernel_ms);
+      if (k2 == 1) time_shape(shapes[order[f]], nullptr, n_paths, full[f]);
+      else time_shape(shapes[order[f]], dF, 0, full[f]);
     }
   float best_ms = 1e30f;
   for (size_t f = 0; f < finalists; ++f)

@@ -85,7 +85,9 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 2000,
     import torch
     P = pdds.Problem(w)
     out = {"workload": w.name, "knots": P.n, "dt": w.dt, "n_plain": n_plain}
-    # plain estimator
+    # plain estimator (launch shape tuned for it first, untimed: short paths
+    # favour small CTAs and units)
+    out["launch_plain"] = pdds.pdds_autotune(P.ctx, n_plain, w.dt, w.seed)
     t_plain, u_plain, steps_plain, k_plain = _assemble_solve(P, n_plain, w.seed)
     # control variate: warm-up, fit, production
     fit = fit_control_variate(P, n0, steps=train_steps)
@@ -99,6 +101,7 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 2000,
     rms_probe = rms(u_probe)
     # statistical error ~ 1/sqrt(N): pick N_cv to match the plain error
     n_cv = int(max(64, round(max(n0, 256) * (rms_probe / rms_plain) ** 2 * 1.1)))
+    out["launch_cv"] = pdds.pdds_autotune(P.ctx, n_cv, w.dt, w.seed + 7)
     t_cv, u_cv, steps_cv, k_cv = _assemble_solve(P, n_cv, w.seed + 7)
     pdds.pdds_set_control_variate(P.ctx, None)
     # the reference itself carries error ~ rms_cv / sqrt(ref_factor * n_plain / n_cv)
