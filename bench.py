@@ -50,8 +50,11 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_2301_05780_gb300", "csrc", "pdds_path.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the path kernel's sources (template header and launch unit)."""
+    h = hashlib.sha256()
+    for f in ("path_kernel.cuh", "pdds_path.cu", "pdds_rbf.cuh", "pdds_mlp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2301_05780_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(name: str):
