@@ -703,7 +703,8 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
 
     // ---- step until enough lanes have exited -----------------------------
     const float h = EXT ? h_l : P.h, sqh = EXT ? sqh_l : P.sqh;
-    const int64_t kmax = EXT ? kmax_l : P.kmax;
+    // 32-bit step cap (the API keeps caps below 2^31): one compare per step
+    const int kmax = (int)min(EXT ? kmax_l : P.kmax, (int64_t)0x7fffffff);
     bool exited = false, trunc = false;
     for (;;) {
       if constexpr (CV == 1) {

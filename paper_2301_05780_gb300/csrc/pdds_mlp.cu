@@ -21,34 +21,39 @@
 namespace pdds {
 namespace {
 
-constexpr int kTrainThreads = 128;
+constexpr int kTrainThreads = 64;
 constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 4352, kOffB3 = 4416;
 // shared layout of the training kernel (floats)
 constexpr int kSmW = 4480;                           // theta copy (padded)
-constexpr int kSmArr = kMlpHidden * kTrainThreads;   // one [64][128] activation array
+constexpr int kSmStride = kTrainThreads + 1;        // row stride: rows fall in distinct banks
+constexpr int kSmArr = kMlpHidden * kSmStride;       // one [64][64] activation array (padded)
 constexpr size_t kTrainSmemBytes = (kSmW + 4 * kSmArr + 4 * kTrainThreads) * sizeof(float);
 
 __device__ __forceinline__ float logistic(float a) { return 1.0f / (1.0f + __expf(-a)); }
 
 // Mean-squared-error loss (1/N) sum (v(x_p) - target_p)^2 and its gradient
 // with respect to theta; one thread per point, block partial sums are added
-// to grad with atomics.
+// to grad with atomics.  Every dot product runs as four independent FMA chains
+// (four outputs, or four parameters, at a time): with 64-point blocks there
+// are few warps per SM, so latency, not issue, is the limit.
 __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(
     const float* __restrict__ theta, const float* __restrict__ xy, const float* __restrict__ tgt,
     int64_t npts, float scale, float* __restrict__ grad, double* __restrict__ loss) {
   extern __shared__ float sm[];
   float* T = sm;                       // theta
-  float* H1 = sm + kSmW;               // [64][128] SiLU(a1)
-  float* D1 = H1 + kSmArr;             // [64][128] SiLU'(a1), later dL/da1
-  float* H2 = D1 + kSmArr;             // [64][128] SiLU(a2)
-  float* G2 = H2 + kSmArr;             // [64][128] dL/da2
-  float* PX = G2 + kSmArr;             // [128] x, y, dL/dv
+  float* H1 = sm + kSmW;               // [64][P] SiLU(a1)
+  float* D1 = H1 + kSmArr;             // [64][P] SiLU'(a1), later dL/da1
+  float* H2 = D1 + kSmArr;             // [64][P] SiLU(a2)
+  float* G2 = H2 + kSmArr;             // [64][P] dL/da2
+  float* PX = G2 + kSmArr;             // [P] x, y, dL/dv
   float* PY = PX + kTrainThreads;
   float* DV = PY + kTrainThreads;
   float* RL = DV + kTrainThreads;      // squared residuals
+  constexpr int P = kTrainThreads;
+  constexpr int S = kSmStride;
   const int tid = threadIdx.x;
-  for (int i = tid; i < kMlpParams; i += kTrainThreads) T[i] = theta[i];
-  const int64_t p = (int64_t)blockIdx.x * kTrainThreads + tid;
+  for (int i = tid; i < kMlpParams; i += P) T[i] = theta[i];
+  const int64_t p = (int64_t)blockIdx.x * P + tid;
   const bool valid = p < npts;
   const float x = valid ? xy[2 * p] : 0.f, y = valid ? xy[2 * p + 1] : 0.f;
   PX[tid] = x;
@@ -57,48 +62,62 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(
   for (int u = 0; u < kMlpHidden; ++u) {
     const float a = fmaf(T[kOffW1 + 2 * u], x, fmaf(T[kOffW1 + 2 * u + 1], y, T[kOffB1 + u]));
     const float s = logistic(a);
-    H1[u * kTrainThreads + tid] = valid ? a * s : 0.f;
-    D1[u * kTrainThreads + tid] = s * (1.f + a * (1.f - s));
+    H1[u * S + tid] = valid ? a * s : 0.f;
+    D1[u * S + tid] = s * (1.f + a * (1.f - s));
   }
   float v = T[kOffB3];
-  for (int o = 0; o < kMlpHidden; ++o) {
-    float a = T[kOffB2 + o];
-    const float* w = T + kOffW2 + o * kMlpHidden;
-    for (int u = 0; u < kMlpHidden; ++u) a = fmaf(w[u], H1[u * kTrainThreads + tid], a);
-    const float s = logistic(a);
-    const float h = a * s;
-    H2[o * kTrainThreads + tid] = h;
-    G2[o * kTrainThreads + tid] = T[kOffW3 + o] * s * (1.f + a * (1.f - s));
-    v = fmaf(T[kOffW3 + o], h, v);
+  for (int o = 0; o < kMlpHidden; o += 4) {
+    float a[4] = {T[kOffB2 + o], T[kOffB2 + o + 1], T[kOffB2 + o + 2], T[kOffB2 + o + 3]};
+    for (int u = 0; u < kMlpHidden; ++u) {
+      const float h1 = H1[u * S + tid];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = fmaf(T[kOffW2 + (o + q) * kMlpHidden + u], h1, a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float s = logistic(a[q]);
+      const float h = a[q] * s;
+      H2[(o + q) * S + tid] = h;
+      G2[(o + q) * S + tid] = T[kOffW3 + o + q] * s * (1.f + a[q] * (1.f - s));
+      v = fmaf(T[kOffW3 + o + q], h, v);
+    }
   }
   const float r = valid ? v - tgt[p] : 0.f;
   const float dv = scale * r;  // scale = 2 / N
   DV[tid] = dv;
   RL[tid] = r * r;
-  for (int o = 0; o < kMlpHidden; ++o) G2[o * kTrainThreads + tid] *= dv;
+  for (int o = 0; o < kMlpHidden; ++o) G2[o * S + tid] *= dv;
   // dL/da1 = SiLU'(a1) * sum_o W2[o][u] dL/da2[o]
-  for (int u = 0; u < kMlpHidden; ++u) {
-    float s = 0.f;
-    for (int o = 0; o < kMlpHidden; ++o)
-      s = fmaf(T[kOffW2 + o * kMlpHidden + u], G2[o * kTrainThreads + tid], s);
-    D1[u * kTrainThreads + tid] *= s;
+  for (int u = 0; u < kMlpHidden; u += 4) {
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int o = 0; o < kMlpHidden; ++o) {
+      const float g = G2[o * S + tid];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = fmaf(T[kOffW2 + o * kMlpHidden + u + q], g, t[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) D1[(u + q) * S + tid] *= t[q];
   }
   __syncthreads();
-  // block reductions over the 128 points, one parameter group per thread
-  for (int i = tid; i < kMlpHidden * kMlpHidden; i += kTrainThreads) {
-    const int o = i / kMlpHidden, u = i % kMlpHidden;
-    float s = 0.f;
-    for (int q = 0; q < kTrainThreads; ++q)
-      s = fmaf(G2[o * kTrainThreads + q], H1[u * kTrainThreads + q], s);
-    atomicAdd(grad + kOffW2 + i, s);
-  }
-  if (tid < kMlpHidden) {
-    const int o = tid;
+  // block reductions over the P points: thread tid owns row o = tid of the
+  // 64x64 weight gradient, four columns at a time
+  {
+    const int o = tid;  // P == kMlpHidden
+    for (int u = 0; u < kMlpHidden; u += 4) {
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < P; ++q) {
+        const float g = G2[o * S + q];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) t[c] = fmaf(g, H1[(u + c) * S + q], t[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) atomicAdd(grad + kOffW2 + o * kMlpHidden + u + c, t[c]);
+    }
     float gb2 = 0.f, gw3 = 0.f, gw10 = 0.f, gw11 = 0.f, gb1 = 0.f;
-    for (int q = 0; q < kTrainThreads; ++q) {
-      gb2 += G2[o * kTrainThreads + q];
-      gw3 = fmaf(DV[q], H2[o * kTrainThreads + q], gw3);
-      const float d = D1[o * kTrainThreads + q];
+    for (int q = 0; q < P; ++q) {
+      gb2 += G2[o * S + q];
+      gw3 = fmaf(DV[q], H2[o * S + q], gw3);
+      const float d = D1[o * S + q];
       gw10 = fmaf(d, PX[q], gw10);
       gw11 = fmaf(d, PY[q], gw11);
       gb1 += d;
@@ -109,14 +128,15 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(
     atomicAdd(grad + kOffW1 + 2 * o + 1, gw11);
     atomicAdd(grad + kOffB1 + o, gb1);
   }
-  if (tid == kMlpHidden) {
+  if (tid == 0) {
     float gb3 = 0.f;
     double l = 0.0;
-    for (int q = 0; q < kTrainThreads; ++q) { gb3 += DV[q]; l += (double)RL[q]; }
+    for (int q = 0; q < P; ++q) { gb3 += DV[q]; l += (double)RL[q]; }
     atomicAdd(grad + kOffB3, gb3);
     atomicAdd(loss, l / (double)npts);
   }
 }
+static_assert(kTrainThreads == kMlpHidden, "one weight-gradient row per thread");
 
 // Adam (Kingma & Ba 2015) with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t.
 __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ grad,
