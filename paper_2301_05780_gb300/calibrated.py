@@ -24,6 +24,7 @@ import numpy as np
 
 from . import pdds
 from . import workloads as W
+from .cv import tabulate_gradient
 
 
 def _sync_ms(fn):
@@ -110,17 +111,7 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
             pdds.pdds_set_control_variate(P.ctx, theta)
             ttab = 0.0
         else:
-            def tabulate():
-                nx = 2 * w.grid["Hx"] * w.grid["m"] + 1
-                ny = 2 * w.grid["Hy"] * w.grid["m"] + 1
-                gx = torch.linspace(w.grid["x0"], w.grid["x1"], nx, dtype=torch.float32,
-                                    device=dev)
-                gy = torch.linspace(w.grid["y0"], w.grid["y1"], ny, dtype=torch.float32,
-                                    device=dev)
-                pts = torch.stack(torch.meshgrid(gx, gy, indexing="xy"), dim=-1).reshape(-1, 2)
-                _, grad = pdds.pdds_mlp_eval(theta, pts.contiguous())
-                pdds.pdds_set_control_variate_grid(P.ctx, grad.reshape(ny, nx, 2))
-            _, ttab = _sync_ms(tabulate)
+            _, ttab = _sync_ms(lambda: tabulate_gradient(P.ctx, theta, w.grid, dev))
         out["fit"] = {"ms": tfit + ttab, "steps": train_steps, "final_loss": float(hist[-1]),
                       "cv_kind": cv_kind}
 

@@ -747,6 +747,10 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           }
         }
       } else if (alive && !exited) {
+       // two Philox pairs (four steps) between exit checks of the warp
+#pragma unroll 1
+       for (int pair = 0; pair < 2; ++pair) {
+        if (exited) break;
         const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.key0,
                                       P.key1);
         float z[4];
@@ -791,6 +795,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             if (!exited && n >= kmax) { exited = true; trunc = true; }
           }
         }
+       }
       }
       const unsigned ex = __ballot_sync(kFull, alive && exited);
       const unsigned stepping = __ballot_sync(kFull, alive && !exited);

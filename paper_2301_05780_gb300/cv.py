@@ -62,6 +62,21 @@ def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float =
     return CVResult(theta, warm_ms, train_ms, hist[0])
 
 
+def tabulate_gradient(ctx, theta, grid: dict, dev, per_interval: int = 2):
+    """Sec. 4.2's look-up table of grad u0: grad v_theta at the nodes of a grid
+    over Omega with `per_interval` nodes per knot spacing, evaluated by the
+    library's in-path routine and attached to ctx as the control variate."""
+    import torch
+    nx = per_interval * grid["Hx"] * grid["m"] + 1
+    ny = per_interval * grid["Hy"] * grid["m"] + 1
+    gx = torch.linspace(grid["x0"], grid["x1"], nx, dtype=torch.float32, device=dev)
+    gy = torch.linspace(grid["y0"], grid["y1"], ny, dtype=torch.float32, device=dev)
+    pts = torch.stack(torch.meshgrid(gx, gy, indexing="xy"), dim=-1).reshape(-1, 2)
+    _, grad = pdds.pdds_mlp_eval(theta, pts.contiguous())
+    pdds.pdds_set_control_variate_grid(ctx, grad.reshape(ny, nx, 2))
+    return nx, ny
+
+
 def _assemble_solve(P: pdds.Problem, N: int, seed: int):
     """Assembly (kernel time from CUDA events) + solve; returns (ms, u, steps)."""
     import torch
@@ -103,6 +118,10 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 2000,
     n_cv = int(max(64, round(max(n0, 256) * (rms_probe / rms_plain) ** 2 * 1.1)))
     out["launch_cv"] = pdds.pdds_autotune(P.ctx, n_cv, w.dt, w.seed + 7)
     t_cv, u_cv, steps_cv, k_cv = _assemble_solve(P, n_cv, w.seed + 7)
+    # the same network as Sec. 4.2's look-up table: four table reads per step
+    t_tab_build = _ms(lambda: tabulate_gradient(P.ctx, fit.theta, w.grid, P.dev))
+    out["launch_cv_table"] = pdds.pdds_autotune(P.ctx, n_cv, w.dt, w.seed + 11)
+    t_tab, u_tab, steps_tab, k_tab = _assemble_solve(P, n_cv, w.seed + 11)
     pdds.pdds_set_control_variate(P.ctx, None)
     # the reference itself carries error ~ rms_cv / sqrt(ref_factor * n_plain / n_cv)
     out.update({
@@ -112,7 +131,12 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 2000,
                "assembly_solve_ms": t_cv, "kernel_ms": k_cv, "path_steps": steps_cv,
                "rms_vs_ref": rms(u_cv), "final_train_loss": float(fit.loss_history[-1]),
                "total_ms": fit.warmup_ms + fit.train_ms + t_cv},
+        "cv_table": {"table_ms": t_tab_build, "n_cv": n_cv, "assembly_solve_ms": t_tab,
+                     "kernel_ms": k_tab, "path_steps": steps_tab, "rms_vs_ref": rms(u_tab),
+                     "total_ms": fit.warmup_ms + fit.train_ms + t_tab_build + t_tab},
         "speedup_time_to_equal_error": t_plain / (fit.warmup_ms + fit.train_ms + t_cv),
+        "speedup_time_to_equal_error_table": t_plain / (fit.warmup_ms + fit.train_ms +
+                                                       t_tab_build + t_tab),
         # var ~ rms^2 N: (rms_plain^2 n_plain) / (rms_probe^2 n_probe)
         "variance_reduction_estimate": (rms_plain / rms_probe) ** 2 * n_plain / max(n0, 256),
     })
