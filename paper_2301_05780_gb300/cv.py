@@ -39,8 +39,10 @@ def _ms(fn):
 
 
 def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float = 3e-3,
-                        seed_offset: int = 7919) -> CVResult:
-    """Phase I on P's grid with n0 paths per knot, then fit v_theta to u0."""
+                        seed_offset: int = 7919, max_points: int = 16384) -> CVResult:
+    """Phase I on P's grid with n0 paths per knot, then fit v_theta to u0 at
+    (at most max_points, seeded) knots: u0 is smooth at the network's scale,
+    so a subset trains it as well as every knot for a fraction of the cost."""
     import torch
     w = P.w
     dev = P.dev
@@ -52,6 +54,10 @@ def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float =
     warm_ms = _ms(warm)
     xy = torch.tensor(pdds.pdds_knot_coords(P.ctx), dtype=torch.float32, device=dev)
     u0 = P.u.to(torch.float32)
+    if P.n > max_points:
+        g = torch.Generator(device="cpu").manual_seed(int(w.seed) & 0x7fffffff)
+        pick = torch.randperm(P.n, generator=g)[:max_points].to(dev)
+        xy, u0 = xy[pick].contiguous(), u0[pick].contiguous()
     theta = torch.tensor(W.mlp_init(), dtype=torch.float32, device=dev)
     hist = [None]
 
@@ -89,7 +95,7 @@ def _assemble_solve(P: pdds.Problem, N: int, seed: int):
     return t, P.u.clone(), st["path_steps"], st["path_kernel_ms"]
 
 
-def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 2000,
+def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 1000,
           ref_factor: int = 4) -> dict:
     """Time to equal interfacial statistical error, plain vs control variate.
 
