@@ -829,14 +829,20 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           ov[3] = (tb[2] + sh[3]) - Y;
         }
       }
+      // smallest positive overshoot (ties to the earlier side), else (a path
+      // truncated inside the box) the largest; the running best stays in a
+      // register so the overshoots need no indexed (local-memory) array
       side = -1;
+      float best = 0.f;
 #pragma unroll
       for (int o = 0; o < 4; ++o)
-        if (ov[o] > 0.f && (side < 0 || ov[o] < ov[side])) side = o;
+        if (ov[o] > 0.f && (side < 0 || ov[o] < best)) { side = o; best = ov[o]; }
       if (side < 0) {
+        side = 0;
+        best = ov[0];
 #pragma unroll
-        for (int o = 0; o < 4; ++o)
-          if (side < 0 || ov[o] > ov[side]) side = o;
+        for (int o = 1; o < 4; ++o)
+          if (ov[o] > best) { side = o; best = ov[o]; }
       }
       if constexpr (has_c<COEF>()) Yk = __expf(Sx);
       bc = (double)Z;
