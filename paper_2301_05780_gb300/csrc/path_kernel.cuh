@@ -49,14 +49,15 @@ constexpr double kFixedInv = 1.0 / 1073741824.0;       // 2^-30
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplications whose high halves are xored with the other words
 // and the round key; the key advances by two Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// rk: the ten round keys of each key word (the key advanced by the Weyl
+// constants), precomputed on the host so that every round reads them as
+// launch constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20]) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
     const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
   }
   return c;
 }
@@ -714,8 +715,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         const bool go = alive && !exited;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (go) {
-          const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.key0,
-                                        P.key1);
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
           box_muller(r.x, r.y, z[0], z[1]);
           box_muller(r.z, r.w, z[2], z[3]);
         }
@@ -751,8 +751,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
 #pragma unroll 1
        for (int pair = 0; pair < 2; ++pair) {
         if (exited) break;
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.key0,
-                                      P.key1);
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
         float z[4];
         box_muller(r.x, r.y, z[0], z[1]);
         box_muller(r.z, r.w, z[2], z[3]);

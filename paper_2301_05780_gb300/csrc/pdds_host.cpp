@@ -397,6 +397,10 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   kp.records = rec;
   kp.key0 = (uint32_t)seed;
   kp.key1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Philox4x32-10 key schedule (Weyl constants)
+    kp.round_keys[2 * r] = kp.key0 + (uint32_t)r * 0x9E3779B9u;
+    kp.round_keys[2 * r + 1] = kp.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   kp.h = (float)dt;
   kp.sqh = (float)std::sqrt(dt);
   kp.kmax = kmax;

@@ -100,6 +100,7 @@ struct KParams {
   Scratch* scratch;
   PathRecordDev* records;
   uint32_t key0, key1;
+  uint32_t round_keys[20];  // Philox round r: key0 + r W0, key1 + r W1 (rounds 0..9)
   float h, sqh;
   int64_t kmax;
   int32_t max_slots;       // accumulator slots per stage
