@@ -1,7 +1,7 @@
 // Launch plumbing of the persistent path kernel: per-knot unit and record
 // prefixes, the per-problem unit prefix, the finalize kernel (Eq. 24-25) and
 // the dispatch to the kernel variants, which are instantiated in
-// pdds_path_{em,cv,ext,ext_cv}.cu so that they compile in parallel.
+// pdds_path_{em,cv,cvt,ext,ext_cv,ext_cvt}.cu so that they compile in parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
