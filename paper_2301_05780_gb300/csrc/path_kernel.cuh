@@ -67,6 +67,11 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -81,13 +86,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
   const float s32 = 2.3283064365386963e-10f;  // 2^-32
   const float ua = fmaf(__uint2float_rn(a), s32, 0.5f * s32);
-  const float ub = __uint_as_float(0x3f800000u | (b >> 9)) - 0.99999994039535522f;
   const float rho = sqrt_approx(-1.38629436111989061f * lg2_approx(ua));  // -2 ln u_a
-  const float r = ub - rintf(ub);
+  // u_b - 1/2 in [-1/2, 1/2) (both steps exact): cos and sin of 2 pi u_b are
+  // minus those of 2 pi (u_b - 1/2), absorbed by the sign of rho
+  const float r = (__uint_as_float(0x3f800000u | (b >> 9)) - 1.5f) + 5.9604644775390625e-8f;
   float sn, cs;
   __sincosf(kTwoPi * r, &sn, &cs);
-  z0 = rho * cs;
-  z1 = rho * sn;
+  z0 = -rho * cs;
+  z1 = -rho * sn;
 }
 
 // sin(2 pi t), cos(2 pi t) for any t (argument reduced to [-1/2, 1/2]).
@@ -289,10 +295,11 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
       sincos_2pi(0.5f * x, sx, cx);
       sincos_2pi(0.5f * y, sy, cy);
     }
-    const float u = fmaf(sx, cy, x * y);
+    const float sxcy = sx * cy;
+    const float u = fmaf(x, y, sxcy);
     const float ux = fmaf(pi * cx, cy, y);
     const float uy = fmaf(-pi * sx, sy, x);
-    const float lap = -2.0f * pi * pi * sx * cy;
+    const float lap = (-2.0f * pi * pi) * sxcy;
     s = 1.41421356237309505f;
     dx = 2.0f * sy * cy;
     dy = fmaf(-2.0f * sx, sx, 1.0f);
@@ -704,6 +711,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
 
     // ---- step until enough lanes have exited -----------------------------
     const float h = EXT ? h_l : P.h, sqh = EXT ? sqh_l : P.sqh;
+    const float hl2 = h * 1.44269504088896341f;  // S is kept in log2 units: Y = 2^S
     // 32-bit step cap (the API keeps caps below 2^31): one compare per step
     const int kmax = (int)min(EXT ? kmax_l : P.kmax, (int64_t)0x7fffffff);
     bool exited = false, trunc = false;
@@ -730,9 +738,9 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
                          s, ddx, ddy, c, f);
             const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
             float Yw = 1.0f;
-            if constexpr (has_c<COEF>()) Yw = __expf(Sx);
+            if constexpr (has_c<COEF>()) Yw = ex2_approx(Sx);
             if constexpr (has_f<COEF>()) Z = fmaf(-f * Yw, h, Z);
-            if constexpr (has_c<COEF>()) Sx = fmaf(c, h, Sx);
+            if constexpr (has_c<COEF>()) Sx = fmaf(c, hl2, Sx);
             XI = fmaf(-Yw * s, fmaf(gx, dWx, gy * dWy), XI);
             const float ssh = s * sqh;
             X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
@@ -764,9 +772,9 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
                          s, ddx, ddy, c, f);
             float Yw = 1.0f;
             if constexpr (has_c<COEF>()) {
-              Yw = __expf(Sx);
+              Yw = ex2_approx(Sx);
               Z = fmaf(-f * Yw, h, Z);  // dZ = -f Y dt
-              Sx = fmaf(c, h, Sx);      // dY = c Y dt, Y = exp(S)
+              Sx = fmaf(c, hl2, Sx);    // dY = c Y dt, Y = 2^S with S = log2(e) int c dt
             } else if constexpr (has_f<COEF>()) {
               Z = fmaf(-f, h, Z);       // c = 0: Y = 1
             }
@@ -843,7 +851,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         for (int o = 1; o < 4; ++o)
           if (ov[o] > best) { side = o; best = ov[o]; }
       }
-      if constexpr (has_c<COEF>()) Yk = __expf(Sx);
+      if constexpr (has_c<COEF>()) Yk = ex2_approx(Sx);
       bc = (double)Z;
       if constexpr (CV != 0) bc += (double)XI;
       const bool vertical = (side == 0 || side == 2);
