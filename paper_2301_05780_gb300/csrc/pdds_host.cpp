@@ -320,7 +320,7 @@ void sigma_bounds(const pdds_coeffs& cf, const std::vector<float>& sig, double& 
 
 size_t stage_bytes(const pdds_ctx* c) {
   size_t b = pdds::stage_header_bytes() + round_up((size_t)c->geo.max_slots * 8, 128);
-  if (c->coef_id == PDDS_COEF_TABLE) b += 2 * round_up((size_t)c->tile_w * c->tile_h * 4, 128);
+  if (c->coef_id == PDDS_COEF_TABLE) b += round_up((size_t)2 * c->tile_w * c->tile_h * 4, 128);
   return round_up(b, 128);
 }
 
@@ -589,36 +589,37 @@ pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx**
     }
     c->tile_w = (int)round_up((size_t)need_w, 4);
     c->tile_h = need_h;
-    if (c->tile_w > 256 || c->tile_h > 256 || 2 * c->tile_w * c->tile_h * 4 > 96 * 1024) {
+    // the TMA box holds 2 tile_w interleaved floats per row (<= 256)
+    if (c->tile_w > 128 || c->tile_h > 256 || 2 * c->tile_w * c->tile_h * 4 > 96 * 1024) {
       free_ctx(c);
       return fail(nullptr, PDDS_EINVAL,
-                  "create: coefficient tile per patch exceeds 256x256 nodes / 96 KB");
+                  "create: coefficient tile per patch exceeds 128x256 nodes / 96 KB");
     }
     auto enc = get_encode_fn();
     if (!enc) {
       free_ctx(c);
       return fail(nullptr, PDDS_ECUDA, "create: cuTensorMapEncodeTiled unavailable");
     }
-    const size_t pitch = round_up((size_t)cf->tab_nx, 4);  // 16-byte row pitch
-    std::vector<float> padded(2 * pitch * cf->tab_ny, 0.0f);
+    // one table of interleaved (s, c) pairs per node, rows padded to 16 bytes
+    const size_t pitch = round_up((size_t)2 * cf->tab_nx, 4);
+    std::vector<float> padded(pitch * cf->tab_ny, 0.0f);
     for (int j = 0; j < cf->tab_ny; ++j)
       for (int i = 0; i < cf->tab_nx; ++i) {
-        padded[j * pitch + i] = sig_host[(size_t)j * cf->tab_nx + i];
-        padded[(cf->tab_ny + j) * pitch + i] = c_host[(size_t)j * cf->tab_nx + i];
+        padded[j * pitch + 2 * i] = sig_host[(size_t)j * cf->tab_nx + i];
+        padded[j * pitch + 2 * i + 1] = c_host[(size_t)j * cf->tab_nx + i];
       }
     if ((e = dalloc(&c->d_tab, padded.size())) != cudaSuccess) return bail(e, "table alloc");
     if ((e = cudaMemcpy(c->d_tab, padded.data(), padded.size() * 4, cudaMemcpyHostToDevice)) !=
         cudaSuccess)
       return bail(e, "table upload");
-    CUtensorMap maps[2];
-    for (int f = 0; f < 2; ++f) {
-      const cuuint64_t dims[2] = {(cuuint64_t)cf->tab_nx, (cuuint64_t)cf->tab_ny};
+    CUtensorMap maps[1];
+    {
+      const cuuint64_t dims[2] = {(cuuint64_t)(2 * cf->tab_nx), (cuuint64_t)cf->tab_ny};
       const cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
-      const cuuint32_t box[2] = {(cuuint32_t)c->tile_w, (cuuint32_t)c->tile_h};
+      const cuuint32_t box[2] = {(cuuint32_t)(2 * c->tile_w), (cuuint32_t)c->tile_h};
       const cuuint32_t es[2] = {1, 1};
-      CUresult r = enc(&maps[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                       c->d_tab + (size_t)f * pitch * cf->tab_ny, dims, strides, box, es,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+      CUresult r = enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->d_tab, dims, strides, box,
+                       es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) {
         free_ctx(c);
@@ -1236,7 +1237,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
     CK(c0, cudaMemcpy(c0->d_batch, probs.data(), count * sizeof(ProbDesc), cudaMemcpyHostToDevice));
     const size_t sb = [&] {
       size_t x = pdds::stage_header_bytes() + round_up((size_t)max_slots * 8, 128);
-      if (c0->coef_id == PDDS_COEF_TABLE) x += 2 * round_up((size_t)tw * th * 4, 128);
+      if (c0->coef_id == PDDS_COEF_TABLE) x += round_up((size_t)2 * tw * th * 4, 128);
       return round_up(x, 128);
     }();
     CK(c0, pdds::set_path_kernel_smem(c0->coef_id, false, 0, false, 2 * sb));

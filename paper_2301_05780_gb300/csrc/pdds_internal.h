@@ -54,7 +54,7 @@ struct ProbDesc {
   const int64_t* path_prefix;     // [n+1] records before knot k (records mode)
   double* Gval;
   double* b;
-  const CUtensorMap* tmap;        // TABLE: [2] = sigma, c (device global memory)
+  const CUtensorMap* tmap;        // TABLE: map of the interleaved (sigma, c) table (device)
   int32_t tab_nx, tab_ny;        // TABLE: table nodes
   const int32_t* col;             // CSR column of each value (records mode)
   const double* h_per_knot;       // per-knot steps (extended-exit kernels), or nullptr
