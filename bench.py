@@ -373,6 +373,8 @@ def main():
                     help="skip the CPU-oracle baseline and the end-to-end leg (profiling runs)")
     ap.add_argument("--cv", default="table", choices=["table", "network"],
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
+    ap.add_argument("--train-steps", type=int, default=3000,
+                    help="Adam steps of the e1 pipeline's network fit")
     ap.add_argument("--interp", default="linear", choices=["linear", "rbf"],
                     help="stencil interpolation of the e1 pipeline (Sec. 2.1 RBF or linear)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -493,7 +495,7 @@ def run_e1(args):
     w = workload("e1")
     x = w.extra
     kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
-              rbf=args.interp == "rbf", cv_kind=args.cv)
+              rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps)
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []
@@ -516,7 +518,7 @@ def run_e1(args):
             "config": {"workload": w.name, "knots": out["knots"], "eps": x["eps"],
                        "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
                        "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
-                       "control_variate": args.cv,
+                       "control_variate": args.cv, "train_steps": args.train_steps,
                        "note": "path-steps of the GM pass counted twice for the mixed run"},
             "pipeline": {
                 "phase1": {"ms": out["phase1"]["ms"], "path_steps": out["phase1"]["path_steps"],
