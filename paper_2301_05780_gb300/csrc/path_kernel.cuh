@@ -605,8 +605,16 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // variants hold the MMA fragments of the in-path network: at most 256 threads
 // and two CTAs per SM, i.e. up to 128 registers.  EXT: per-knot steps and the
 // Gobet-Menozzi shift (P.gm).
+// Register caps: 128 for the network variants; 56 for the plain kernels with
+// analytic coefficients (a few bytes of spill, about 1.5 % faster than 64 on
+// the manufactured workload: more warps per SM); 64 for the rest, which spill
+// tens of bytes at 56.
+constexpr int path_kernel_regs(int coef, int cv, bool ext) {
+  return cv == 1 ? 128 : (cv == 0 && !ext && coef != PDDS_COEF_TABLE ? 56 : 64);
+}
 template <int COEF, bool RECORD, int CV, bool EXT>
 __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
+    __maxnreg__(path_kernel_regs(COEF, CV, EXT))
     path_kernel(const __grid_constant__ KParams P) {
   extern __shared__ __align__(128) char smem_raw[];
   const int lane = threadIdx.x & 31;
