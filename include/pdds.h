@@ -314,7 +314,13 @@ pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, const float*
 /* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr)
  * on the loss above; theta (DEVICE) is updated in place; loss_history_host
  * (nullable) receives the loss before each step.  Allocates and frees its own
- * scratch (gradient and Adam moments); synchronizes the stream. */
+ * scratch (gradient, Adam moments, step state, loss history) and a private
+ * stream on which the steps run as a replayed CUDA graph, ordered after the
+ * work already queued on cuda_stream; synchronizes.  One kernel launch per
+ * step: 64-point tiles on at most two CTAs per SM, FP32 throughout, the
+ * CTA partial gradients added with FP32 atomics (the summation order, and so
+ * the last bits, vary from run to run).
+ * Errors: EINVAL (NULL pointer, npts < 1, steps < 1, lr <= 0), ECUDA. */
 pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target, int64_t npts,
                            int32_t steps, double lr, double* loss_history_host,
                            void* cuda_stream);

@@ -10,7 +10,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <string>
 #include <vector>
 
@@ -21,135 +23,317 @@
 namespace pdds {
 namespace {
 
-constexpr int kTrainThreads = 64;
 constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 4352, kOffB3 = 4416;
-// shared layout of the training kernel (floats)
-constexpr int kSmW = 4480;                           // theta copy (padded)
-constexpr int kSmStride = kTrainThreads + 1;        // row stride: rows fall in distinct banks
-constexpr int kSmArr = kMlpHidden * kSmStride;       // one [64][64] activation array (padded)
-constexpr size_t kTrainSmemBytes = (kSmW + 4 * kSmArr + 4 * kTrainThreads) * sizeof(float);
+
+// ------------------------------------------------------------- training
+// One launch = one full-batch gradient of the loss (1/N) sum_p (v(x_p) -
+// target_p)^2 and, in the training variant, the Adam step that follows it.
+//
+// A CTA takes tiles of 64 points; 256 threads form a 16 x 16 grid, thread
+// (ty, tx) owning a 4 x 4 micro-tile (rows 4ty.., columns 4tx..) of each
+// 64 x 64 product of the tile:
+//   forward   a2[p][o] = b2[o] + sum_u h1[p][u] W2[o][u]
+//   backward  dW2[o][u] += sum_p g2[p][o] h1[p][u]      (kept in registers
+//                                                       across the CTA's tiles)
+//             dh1[p][u] = sum_o g2[p][o] W2[o][u]
+// with h1 and g2 = dL/da2 staged in shared memory (rows padded to 68 floats:
+// the two row groups a warp reads fall in different banks).  The CTA's
+// partial gradient is added to grad with FP32 reductions; the CTA that
+// arrives last (a counter, nothing waits) then reads the complete gradient
+// and applies Adam, and clears the gradient and counter for the next launch.
+// The step index lives on the device, so identical launches can be queued.
+constexpr int kTrainThreads = 256;
+constexpr int kTileP = 64;
+constexpr int kLd = 68;
+struct TrainSmem {
+  float W2r[kMlpHidden][kLd];  // W2[o][u]
+  float W2c[kMlpHidden][kLd];  // W2[o][u] at [u][o]
+  float H1[kTileP][kLd];       // SiLU(a1)   [p][u]
+  float G2[kTileP][kLd];       // dL/da2     [p][o]
+  float w1x[kMlpHidden], w1y[kMlpHidden], b1[kMlpHidden], b2[kMlpHidden], w3[kMlpHidden];
+  float b3;
+  float red_b3[16];
+  double red_loss[16];
+  int last;
+};
+constexpr size_t kTrainSmemBytes = sizeof(TrainSmem);
+// the end-of-CTA column sums [5][16][64] are staged over h1 and g2 (adjacent)
+static_assert(offsetof(TrainSmem, G2) == offsetof(TrainSmem, H1) + sizeof(float) * kTileP * kLd,
+              "g2 follows h1");
+static_assert(5 * 16 * 64 <= 2 * kTileP * kLd, "column-sum staging fits in h1 and g2");
+
+// Step state of a training run (device, zeroed before the first step).
+struct TrainState {
+  unsigned count;  // CTAs done with the current launch
+  int t;           // Adam steps completed
+  double p1, p2;   // beta1^t, beta2^t (read from step 2 on)
+};
+
+struct TrainArgs {
+  float* theta;
+  const float* xy;
+  const float* tgt;
+  int64_t npts;
+  float scale;      // 2 / N: d loss / d v
+  double inv_n;     // 1 / N
+  float* grad;      // accumulated gradient (zero on entry)
+  double* loss;     // loss accumulator; training: loss history, indexed by the step
+  // training only
+  float *m, *v;
+  TrainState* st;
+  int steps;
+  float lr, beta1, beta2, eps;
+};
 
 __device__ __forceinline__ float logistic(float a) { return 1.0f / (1.0f + __expf(-a)); }
 
-// Mean-squared-error loss (1/N) sum (v(x_p) - target_p)^2 and its gradient
-// with respect to theta; one thread per point, block partial sums are added
-// to grad with atomics.  Every dot product runs as four independent FMA chains
-// (four outputs, or four parameters, at a time): with 64-point blocks there
-// are few warps per SM, so latency, not issue, is the limit.
-__global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(
-    const float* __restrict__ theta, const float* __restrict__ xy, const float* __restrict__ tgt,
-    int64_t npts, float scale, float* __restrict__ grad, double* __restrict__ loss) {
-  extern __shared__ float sm[];
-  float* T = sm;                       // theta
-  float* H1 = sm + kSmW;               // [64][P] SiLU(a1)
-  float* D1 = H1 + kSmArr;             // [64][P] SiLU'(a1), later dL/da1
-  float* H2 = D1 + kSmArr;             // [64][P] SiLU(a2)
-  float* G2 = H2 + kSmArr;             // [64][P] dL/da2
-  float* PX = G2 + kSmArr;             // [P] x, y, dL/dv
-  float* PY = PX + kTrainThreads;
-  float* DV = PY + kTrainThreads;
-  float* RL = DV + kTrainThreads;      // squared residuals
-  constexpr int P = kTrainThreads;
-  constexpr int S = kSmStride;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < kMlpParams; i += P) T[i] = theta[i];
-  const int64_t p = (int64_t)blockIdx.x * P + tid;
-  const bool valid = p < npts;
-  const float x = valid ? xy[2 * p] : 0.f, y = valid ? xy[2 * p + 1] : 0.f;
-  PX[tid] = x;
-  PY[tid] = y;
-  __syncthreads();
-  for (int u = 0; u < kMlpHidden; ++u) {
-    const float a = fmaf(T[kOffW1 + 2 * u], x, fmaf(T[kOffW1 + 2 * u + 1], y, T[kOffB1 + u]));
-    const float s = logistic(a);
-    H1[u * S + tid] = valid ? a * s : 0.f;
-    D1[u * S + tid] = s * (1.f + a * (1.f - s));
+template <bool ADAM>
+__global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const TrainArgs A) {
+  extern __shared__ __align__(16) unsigned char train_smem[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_smem);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int t = 0;
+  if constexpr (ADAM) {
+    t = __ldcg(&A.st->t);
+    if (t >= A.steps) return;  // a launch queued past the last step
   }
-  float v = T[kOffB3];
-  for (int o = 0; o < kMlpHidden; o += 4) {
-    float a[4] = {T[kOffB2 + o], T[kOffB2 + o + 1], T[kOffB2 + o + 2], T[kOffB2 + o + 3]};
-    for (int u = 0; u < kMlpHidden; ++u) {
-      const float h1 = H1[u * S + tid];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = fmaf(T[kOffW2 + (o + q) * kMlpHidden + u], h1, a[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float s = logistic(a[q]);
-      const float h = a[q] * s;
-      H2[(o + q) * S + tid] = h;
-      G2[(o + q) * S + tid] = T[kOffW3 + o + q] * s * (1.f + a[q] * (1.f - s));
-      v = fmaf(T[kOffW3 + o + q], h, v);
-    }
-  }
-  const float r = valid ? v - tgt[p] : 0.f;
-  const float dv = scale * r;  // scale = 2 / N
-  DV[tid] = dv;
-  RL[tid] = r * r;
-  for (int o = 0; o < kMlpHidden; ++o) G2[o * S + tid] *= dv;
-  // dL/da1 = SiLU'(a1) * sum_o W2[o][u] dL/da2[o]
-  for (int u = 0; u < kMlpHidden; u += 4) {
-    float t[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int o = 0; o < kMlpHidden; ++o) {
-      const float g = G2[o * S + tid];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) t[q] = fmaf(T[kOffW2 + o * kMlpHidden + u + q], g, t[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) D1[(u + q) * S + tid] *= t[q];
-  }
-  __syncthreads();
-  // block reductions over the P points: thread tid owns row o = tid of the
-  // 64x64 weight gradient, four columns at a time
+  const float* th = A.theta;
   {
-    const int o = tid;  // P == kMlpHidden
-    for (int u = 0; u < kMlpHidden; u += 4) {
-      float t[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < P; ++q) {
-        const float g = G2[o * S + q];
+    // all 16 loads of a thread in flight at once (one L2 round trip)
+    constexpr int kPer = kMlpHidden * kMlpHidden / kTrainThreads;
+    float w[kPer];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) t[c] = fmaf(g, H1[(u + c) * S + q], t[c]);
+    for (int q = 0; q < kPer; ++q) w[q] = th[kOffW2 + tid + q * kTrainThreads];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      S.W2r[i >> 6][i & 63] = w[q];
+      S.W2c[i & 63][i >> 6] = w[q];
+    }
+  }
+  if (tid < kMlpHidden) {
+    S.w1x[tid] = th[kOffW1 + 2 * tid];
+    S.w1y[tid] = th[kOffW1 + 2 * tid + 1];
+    S.b1[tid] = th[kOffB1 + tid];
+    S.b2[tid] = th[kOffB2 + tid];
+    S.w3[tid] = th[kOffW3 + tid];
+  }
+  if (tid == 0) S.b3 = th[kOffB3];
+  __syncthreads();
+  const int c0 = 4 * tx, r0 = 4 * ty;
+  float dW2[4][4] = {};                          // o = r0 + i, u = c0 + j
+  float gw1x[4] = {}, gw1y[4] = {}, gb1[4] = {};  // u = c0 + j
+  float gb2[4] = {}, gw3[4] = {};                 // o = c0 + j
+  float gb3 = 0.f;
+  double lsum = 0.0;
+  const int64_t ntiles = (A.npts + kTileP - 1) / kTileP;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p0 = tile * kTileP + r0;
+    float px[4], py[4], pt[4];
+    bool pv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      pv[i] = p0 + i < A.npts;
+      px[i] = pv[i] ? A.xy[2 * (p0 + i)] : 0.f;
+      py[i] = pv[i] ? A.xy[2 * (p0 + i) + 1] : 0.f;
+      pt[i] = pv[i] ? A.tgt[p0 + i] : 0.f;
+    }
+    // h1 = SiLU(W1 x + b1) and SiLU'(a1) of this thread's (p, u) block
+    float d1[4][4];
+    {
+      const float4 wx = *reinterpret_cast<const float4*>(&S.w1x[c0]);
+      const float4 wy = *reinterpret_cast<const float4*>(&S.w1y[c0]);
+      const float4 bb = *reinterpret_cast<const float4*>(&S.b1[c0]);
+      const float cwx[4] = {wx.x, wx.y, wx.z, wx.w}, cwy[4] = {wy.x, wy.y, wy.z, wy.w};
+      const float cb[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float a = fmaf(cwx[j], px[i], fmaf(cwy[j], py[i], cb[j]));
+          const float sg = logistic(a);
+          h[j] = pv[i] ? a * sg : 0.f;
+          d1[i][j] = sg * (1.f + a * (1.f - sg));
+        }
+        *reinterpret_cast<float4*>(&S.H1[r0 + i][c0]) = make_float4(h[0], h[1], h[2], h[3]);
+      }
+    }
+    __syncthreads();
+    // forward: a2 = h1 W2^T + b2 (p = r0 + i, o = c0 + j)
+    float acc[4][4];
+    {
+      const float4 bb = *reinterpret_cast<const float4*>(&S.b2[c0]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = bb.x; acc[i][1] = bb.y; acc[i][2] = bb.z; acc[i][3] = bb.w;
+      }
+    }
+#pragma unroll 8
+    for (int u = 0; u < kMlpHidden; ++u) {
+      const float4 w = *reinterpret_cast<const float4*>(&S.W2c[u][c0]);
+      const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float h = S.H1[r0 + i][u];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(h, wv[j], acc[i][j]);
+      }
+    }
+    // h2, v, the residual, and g2 = dL/da2 = (2/N) r w3 SiLU'(a2)
+    {
+      const float4 w = *reinterpret_cast<const float4*>(&S.w3[c0]);
+      const float cw3[4] = {w.x, w.y, w.z, w.w};
+      const float b3 = S.b3;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float h2[4], sp[4], vp = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float a = acc[i][j];
+          const float sg = logistic(a);
+          h2[j] = a * sg;
+          sp[j] = sg * (1.f + a * (1.f - sg));
+          vp = fmaf(cw3[j], h2[j], vp);
+        }
+        // v: sum over the 16 column groups (lanes with equal ty, one half-warp)
+#pragma unroll
+        for (int off = 1; off < 16; off <<= 1) vp += __shfl_xor_sync(0xffffffffu, vp, off);
+        const float r = pv[i] ? (vp + b3) - pt[i] : 0.f;
+        const float dv = A.scale * r;
+        float g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          g[j] = dv * cw3[j] * sp[j];
+          gb2[j] += g[j];
+          gw3[j] = fmaf(dv, h2[j], gw3[j]);
+        }
+        *reinterpret_cast<float4*>(&S.G2[r0 + i][c0]) = make_float4(g[0], g[1], g[2], g[3]);
+        if (tx == 0) {
+          gb3 += dv;
+          lsum += (double)(r * r);
+        }
+      }
+    }
+    __syncthreads();
+    // dW2[o][u] += sum_p g2[p][o] h1[p][u] (o = r0 + i, u = c0 + j)
+#pragma unroll 8
+    for (int p = 0; p < kTileP; ++p) {
+      const float4 g = *reinterpret_cast<const float4*>(&S.G2[p][r0]);
+      const float4 h = *reinterpret_cast<const float4*>(&S.H1[p][c0]);
+      const float gv[4] = {g.x, g.y, g.z, g.w}, hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dW2[i][j] = fmaf(gv[i], hv[j], dW2[i][j]);
+    }
+    // dh1[p][u] = sum_o g2[p][o] W2[o][u] (p = r0 + i, u = c0 + j), then
+    // da1 = dh1 SiLU'(a1) into the first layer's gradient
+    {
+      float dh[4][4] = {};
+#pragma unroll 8
+      for (int o = 0; o < kMlpHidden; ++o) {
+        const float4 w = *reinterpret_cast<const float4*>(&S.W2r[o][c0]);
+        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float g = S.G2[r0 + i][o];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dh[i][j] = fmaf(g, wv[j], dh[i][j]);
+        }
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) atomicAdd(grad + kOffW2 + o * kMlpHidden + u + c, t[c]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float da = dh[i][j] * d1[i][j];
+          gw1x[j] = fmaf(da, px[i], gw1x[j]);
+          gw1y[j] = fmaf(da, py[i], gw1y[j]);
+          gb1[j] += da;
+        }
     }
-    float gb2 = 0.f, gw3 = 0.f, gw10 = 0.f, gw11 = 0.f, gb1 = 0.f;
-    for (int q = 0; q < P; ++q) {
-      gb2 += G2[o * S + q];
-      gw3 = fmaf(DV[q], H2[o * S + q], gw3);
-      const float d = D1[o * S + q];
-      gw10 = fmaf(d, PX[q], gw10);
-      gw11 = fmaf(d, PY[q], gw11);
-      gb1 += d;
-    }
-    atomicAdd(grad + kOffB2 + o, gb2);
-    atomicAdd(grad + kOffW3 + o, gw3);
-    atomicAdd(grad + kOffW1 + 2 * o, gw10);
-    atomicAdd(grad + kOffW1 + 2 * o + 1, gw11);
-    atomicAdd(grad + kOffB1 + o, gb1);
+    __syncthreads();  // h1 and g2 are overwritten by the next tile
+  }
+  // ---- the CTA's partial gradient into grad
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicAdd(A.grad + kOffW2 + (r0 + i) * kMlpHidden + c0 + j, dW2[i][j]);
+  // column sums over the 16 row groups (staged in the h1 array)
+  float* red = &S.H1[0][0];  // [5][16][64] over h1 and g2
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    red[(0 * 16 + ty) * 64 + c0 + j] = gw1x[j];
+    red[(1 * 16 + ty) * 64 + c0 + j] = gw1y[j];
+    red[(2 * 16 + ty) * 64 + c0 + j] = gb1[j];
+    red[(3 * 16 + ty) * 64 + c0 + j] = gb2[j];
+    red[(4 * 16 + ty) * 64 + c0 + j] = gw3[j];
+  }
+  if (tx == 0) {
+    S.red_b3[ty] = gb3;
+    S.red_loss[ty] = lsum;
+  }
+  __syncthreads();
+  for (int e = tid; e < 5 * 64; e += kTrainThreads) {
+    const int q = e >> 6, c = e & 63;
+    float sum = 0.f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sum += red[(q * 16 + r) * 64 + c];
+    const int off = q == 0 ? kOffW1 + 2 * c : q == 1 ? kOffW1 + 2 * c + 1
+                  : q == 2 ? kOffB1 + c : q == 3 ? kOffB2 + c : kOffW3 + c;
+    atomicAdd(A.grad + off, sum);
   }
   if (tid == 0) {
-    float gb3 = 0.f;
+    float b = 0.f;
     double l = 0.0;
-    for (int q = 0; q < P; ++q) { gb3 += DV[q]; l += (double)RL[q]; }
-    atomicAdd(grad + kOffB3, gb3);
-    atomicAdd(loss, l / (double)npts);
+    for (int r = 0; r < 16; ++r) { b += S.red_b3[r]; l += S.red_loss[r]; }
+    atomicAdd(A.grad + kOffB3, b);
+    atomicAdd(A.loss + t, l * A.inv_n);
   }
-}
-static_assert(kTrainThreads == kMlpHidden, "one weight-gradient row per thread");
-
-// Adam (Kingma & Ba 2015) with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t.
-__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ grad,
-                            float* __restrict__ m, float* __restrict__ v, int n, float lr, float b1,
-                            float b2, float c1, float c2, float eps) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float g = grad[i];
-  const float mi = b1 * m[i] + (1.f - b1) * g;
-  const float vi = b2 * v[i] + (1.f - b2) * g * g;
-  m[i] = mi;
-  v[i] = vi;
-  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  if constexpr (ADAM) {
+    // Last CTA: Adam (Kingma & Ba 2015) with bias corrections 1 - beta^(t+1).
+    __threadfence();  // this thread's reductions before the arrival count
+    __syncthreads();
+    if (tid == 0) S.last = atomicAdd(&A.st->count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!S.last) return;
+    __threadfence();
+    const double p1 = (t ? __ldcg(&A.st->p1) : 1.0) * (double)A.beta1;  // beta^(t+1)
+    const double p2 = (t ? __ldcg(&A.st->p2) : 1.0) * (double)A.beta2;
+    const float c1 = (float)(1.0 - p1), c2 = (float)(1.0 - p2);
+    // every load of a thread issued before the first update (one round trip)
+    constexpr int kPer = (kMlpParams + kTrainThreads - 1) / kTrainThreads;
+    float g[kPer], mo[kPer], vo[kPer], to[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      if (i < kMlpParams) {
+        g[q] = __ldcg(A.grad + i);
+        mo[q] = A.m[i];
+        vo[q] = A.v[i];
+        to[q] = A.theta[i];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      if (i < kMlpParams) {
+        const float mi = A.beta1 * mo[q] + (1.f - A.beta1) * g[q];
+        const float vi = A.beta2 * vo[q] + (1.f - A.beta2) * g[q] * g[q];
+        A.grad[i] = 0.f;
+        A.m[i] = mi;
+        A.v[i] = vi;
+        A.theta[i] = to[q] - A.lr * (mi / c1) / (sqrtf(vi / c2) + A.eps);
+      }
+    }
+    __syncthreads();  // every thread has read the state
+    if (tid == 0) {
+      A.st->count = 0;
+      A.st->t = t + 1;
+      A.st->p1 = p1;
+      A.st->p2 = p2;
+    }
+  }
 }
 
 // theta (FP32) -> the shared-memory image used in-path (BF16 64x64 layer).
@@ -231,19 +415,29 @@ pdds_status mlp_cuda(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return mlp_cuda(e_, #call); \
   } while (0)
 
-cudaError_t grad_pass(const float* theta, const float* xy, const float* tgt, int64_t npts,
-                      float* grad, double* loss, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// CTAs of a gradient launch: one per 64-point tile, at most two per SM (the
+// occupancy the shared-memory footprint allows).
+cudaError_t train_grid(int64_t npts, unsigned* grid) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static bool attr[256] = {};  // per device: the shared-memory opt-in
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    e = cudaFuncSetAttribute(mlp_train_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTrainSmemBytes);
     if (e != cudaSuccess) return e;
-    attr = true;
+    e = cudaFuncSetAttribute(mlp_train_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTrainSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
   }
-  const int64_t blocks = (npts + kTrainThreads - 1) / kTrainThreads;
-  mlp_grad_kernel<<<(unsigned)blocks, kTrainThreads, kTrainSmemBytes, s>>>(
-      theta, xy, tgt, npts, 2.0f / (float)npts, grad, loss);
-  return cudaGetLastError();
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (npts + kTileP - 1) / kTileP;
+  *grid = (unsigned)std::min<int64_t>(tiles, 2 * (int64_t)sms);
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -254,9 +448,21 @@ extern "C" pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, c
     return mlp_fail(PDDS_EINVAL, "mlp_loss_grad: NULL pointer or npts < 1");
   (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned grid = 0;
+  MCK(train_grid(npts, &grid));
   MCK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
   MCK(cudaMemsetAsync(loss, 0, sizeof(double), s));
-  MCK(grad_pass(theta, xy, target, npts, grad, loss, s));
+  TrainArgs a{};
+  a.theta = const_cast<float*>(theta);  // the gradient variant does not write theta
+  a.xy = xy;
+  a.tgt = target;
+  a.npts = npts;
+  a.scale = 2.0f / (float)npts;
+  a.inv_n = 1.0 / (double)npts;
+  a.grad = grad;
+  a.loss = loss;
+  mlp_train_kernel<false><<<grid, kTrainThreads, kTrainSmemBytes, s>>>(a);
+  MCK(cudaGetLastError());
   return PDDS_OK;
 }
 
@@ -267,35 +473,79 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
     return mlp_fail(PDDS_EINVAL, "mlp_train: NULL pointer, npts < 1, steps < 1 or lr <= 0");
   (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  float* buf = nullptr;  // grad, m, v
-  double* hist = nullptr;
-  MCK(cudaMalloc(reinterpret_cast<void**>(&buf), 3 * kMlpParams * sizeof(float)));
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&hist), steps * sizeof(double));
-  if (e != cudaSuccess) { cudaFree(buf); return mlp_cuda(e, "mlp_train history alloc"); }
-  float *grad = buf, *m = buf + kMlpParams, *v = buf + 2 * kMlpParams;
+  unsigned grid = 0;
+  MCK(train_grid(npts, &grid));
+  // scratch: grad, m, v (FP32), the step state, the loss history
+  const size_t fbytes = 3 * kMlpParams * sizeof(float);
+  const size_t sbytes = (fbytes + 15) / 16 * 16;
+  const size_t bytes = sbytes + sizeof(TrainState) + (size_t)steps * sizeof(double);
+  char* buf = nullptr;
+  MCK(cudaMalloc(reinterpret_cast<void**>(&buf), bytes));
+  float* f = reinterpret_cast<float*>(buf);
+  TrainArgs a{};
+  a.theta = theta;
+  a.xy = xy;
+  a.tgt = target;
+  a.npts = npts;
+  a.scale = 2.0f / (float)npts;
+  a.inv_n = 1.0 / (double)npts;
+  a.grad = f;
+  a.m = f + kMlpParams;
+  a.v = f + 2 * kMlpParams;
+  a.st = reinterpret_cast<TrainState*>(buf + sbytes);
+  a.loss = reinterpret_cast<double*>(buf + sbytes + sizeof(TrainState));
+  a.steps = steps;
+  a.lr = (float)lr;
+  a.beta1 = 0.9f;
+  a.beta2 = 0.999f;
+  a.eps = 1e-8f;
   auto run = [&]() -> cudaError_t {
-    cudaError_t r;
-    if ((r = cudaMemsetAsync(buf + kMlpParams, 0, 2 * kMlpParams * sizeof(float), s))) return r;
-    if ((r = cudaMemsetAsync(hist, 0, steps * sizeof(double), s))) return r;
-    const double b1 = 0.9, b2 = 0.999;
-    for (int t = 1; t <= steps; ++t) {
-      if ((r = cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s))) return r;
-      if ((r = grad_pass(theta, xy, target, npts, grad, hist + (t - 1), s))) return r;
-      adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(
-          theta, grad, m, v, kMlpParams, (float)lr, (float)b1, (float)b2,
-          (float)(1.0 - std::pow(b1, t)), (float)(1.0 - std::pow(b2, t)), 1e-8f);
-      if ((r = cudaGetLastError())) return r;
-    }
+    cudaError_t r = cudaMemsetAsync(buf, 0, bytes, s);
+    if (r != cudaSuccess) return r;
+    // The steps run as a CUDA graph of 64 identical launches replayed
+    // ceil(steps / 64) times on a private stream (the step index is read on
+    // the device; launches past the last step return at once): one graph
+    // launch per 64 steps instead of one kernel launch per step.
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto body = [&]() -> cudaError_t {
+      cudaError_t q;
+      if ((q = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) return q;
+      if ((q = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return q;
+      if ((q = cudaEventRecord(ev, s))) return q;
+      if ((q = cudaStreamWaitEvent(cs, ev, 0))) return q;
+      const int chunk = std::min(steps, 64);
+      if ((q = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) return q;
+      for (int k = 0; k < chunk; ++k)
+        mlp_train_kernel<true><<<grid, kTrainThreads, kTrainSmemBytes, cs>>>(a);
+      cudaError_t lq = cudaGetLastError();
+      q = cudaStreamEndCapture(cs, &graph);
+      if (lq) return lq;
+      if (q) return q;
+      if ((q = cudaGraphInstantiate(&exec, graph, 0))) return q;
+      for (int done = 0; done < steps; done += chunk)
+        if ((q = cudaGraphLaunch(exec, cs))) return q;
+      if ((q = cudaEventRecord(ev, cs))) return q;
+      return cudaStreamWaitEvent(s, ev, 0);
+    };
+    r = body();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (r == cudaSuccess && cs) r = cudaStreamSynchronize(cs);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+    if (r != cudaSuccess) return r;
     if (loss_history_host) {
-      if ((r = cudaMemcpyAsync(loss_history_host, hist, steps * sizeof(double),
-                               cudaMemcpyDeviceToHost, s)))
-        return r;
+      r = cudaMemcpyAsync(loss_history_host, a.loss, steps * sizeof(double),
+                          cudaMemcpyDeviceToHost, s);
+      if (r != cudaSuccess) return r;
     }
     return cudaStreamSynchronize(s);
   };
-  e = run();
+  cudaError_t e = run();
   cudaFree(buf);
-  cudaFree(hist);
   if (e != cudaSuccess) return mlp_cuda(e, "mlp_train");
   return PDDS_OK;
 }

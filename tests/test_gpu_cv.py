@@ -48,6 +48,53 @@ def test_mlp_loss_grad_matches_oracle(orc):
     assert np.linalg.norm(gg - g_o) <= 1e-4 * np.linalg.norm(g_o)
 
 
+def test_mlp_loss_grad_many_tiles_per_cta(orc):
+    """40,017 points: more 64-point tiles than the launch has CTAs (two per
+    SM), so every CTA accumulates several tiles before its reductions; the
+    last tile is ragged."""
+    rng = np.random.default_rng(11)
+    th32 = (W.mlp_init() * rng.uniform(0.5, 1.5, orc.MLP_NPARAM)).astype(np.float32)
+    xy = rng.uniform(-1, 1, size=(40017, 2)).astype(np.float32)
+    tgt = (np.cos(2 * xy[:, 0]) + xy[:, 1] ** 2).astype(np.float32)
+    loss_o, g_o = orc.mlp_loss_grad(th32.astype(np.float64), xy.astype(np.float64),
+                                    tgt.astype(np.float64))
+    loss, g = pdds.pdds_mlp_loss_grad(dev32(th32), dev32(xy), dev32(tgt))
+    assert abs(loss.item() - loss_o) <= 1e-5 * loss_o
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g_o) <= 1e-4 * np.linalg.norm(g_o)
+
+
+def test_mlp_train_follows_oracle_adam(orc):
+    """pdds_mlp_train (the gradient, its reductions and the Adam step of the
+    last CTA, the step index kept on the device) against the oracle's FP64
+    gradient and Adam step, 12 steps on 1013 points (a ragged last tile): the
+    loss history, and the parameter moves where the gradient stays well above
+    FP32 rounding (elsewhere Adam's normalised step amplifies rounding)."""
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(0, 1, size=(1013, 2)).astype(np.float32)
+    tgt = (np.sin(3 * xy[:, 0]) * xy[:, 1]).astype(np.float32)
+    th0 = W.mlp_init().astype(np.float32).astype(np.float64)
+    steps, lr = 12, 3e-3
+    th, m, v = th0.copy(), np.zeros_like(th0), np.zeros_like(th0)
+    hist_o, grads = [], []
+    for t in range(1, steps + 1):
+        loss, g = orc.mlp_loss_grad(th, xy.astype(np.float64), tgt.astype(np.float64))
+        hist_o.append(loss)
+        grads.append(np.abs(g))
+        orc.adam_step(th, g, m, v, t, lr=lr)
+    thg = dev32(th0)
+    hist = pdds.pdds_mlp_train(thg, dev32(xy), dev32(tgt), steps=steps, lr=lr)
+    np.testing.assert_allclose(hist, hist_o, rtol=1e-4)
+    G = np.array(grads)
+    robust = (G > 1e-3 * G.max(axis=1, keepdims=True)).all(axis=0)
+    assert robust.mean() > 0.5, robust.mean()
+    d_o = th - th0
+    d_g = thg.cpu().numpy().astype(np.float64) - th0
+    err = np.abs(d_g - d_o)[robust].max()
+    assert err <= 0.02 * lr, err
+    assert np.abs(d_g - d_o).max() <= 2 * steps * lr + 1e-6
+
+
 def test_mlp_inpath_eval_matches_oracle(orc, trained_theta):
     """The warp-batched BF16 MMA evaluation (also used inside the path kernel)
     against the FP64 network: 1e-2 of the gradient scale (BF16 operands)."""
