@@ -57,10 +57,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
-    """DRAM bytes per launch of the path kernel from the committed ncu summary,
-    if the summary was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "path_kernel_cfg2_ncu.txt")
+# Committed ncu summary of each single-launch workload's path kernel.
+PROFILES = {"cfg2": "path_kernel_cfg2_ncu.txt", "cfg4": "path_kernel_cfg4_tabulated_ncu.txt"}
+
+
+def profiled_traffic(config: str):
+    """DRAM bytes per launch of the path kernel from the committed ncu summary
+    of this workload, if the summary was taken on the current kernel source;
+    else None."""
+    if config not in PROFILES:
+        return None
+    p = os.path.join(ROOT, "profiles", PROFILES[config])
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -170,14 +177,18 @@ def workload(name: str):
 
 
 # ------------------------------------------------------------------ CPU arm
-def oracle_sample(w, rows_wanted: int, threads: int):
+def oracle_sample(w, rows_wanted: int, threads: int, frac: float = 1.0):
     """Times the FP64 oracle on `rows_wanted` evenly spaced rows of w at the
-    full per-knot budget; returns (path_steps, seconds, rows)."""
+    per-knot budget (times frac, at least one path); returns (path_steps,
+    seconds, rows)."""
     import oracle
-    O = oracle.Problem(w.grid, w.coef_id, w.params)
+    tabs = w.tables if w.tables is not None else (None, None)
+    O = oracle.Problem(w.grid, w.coef_id, w.params, sigma_tab=tabs[0], c_tab=tabs[1])
     rows = np.linspace(0, O.n - 1, rows_wanted).round().astype(np.int32)
+    N = w.budgets(O.n) if w.budget_seed is not None else np.full(O.n, w.n_paths, np.int64)
+    N = np.maximum(1, np.round(N * frac)).astype(np.int64)
     t0 = time.perf_counter()
-    _, _, st, _ = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, rows=rows, threads=threads)
+    _, _, st, _ = O.assemble(N, w.dt, w.seed, w.k_max, rows=rows, threads=threads)
     return int(st[0]), time.perf_counter() - t0, rows
 
 
@@ -193,6 +204,28 @@ def cpu_baseline(w, budget_s: float = 15.0):
             "sample": f"{len(rows)} evenly spaced rows of {w.name} at N={w.n_paths}, "
                       f"dt={w.dt:g} ({steps:.3e} path-steps in {secs:.1f} s, FP64, "
                       f"{threads} threads)"}
+
+
+def cpu_baseline_batch(ws, budget_s: float = 15.0):
+    """The oracle on `threads` evenly spaced rows of every problem of a batch,
+    each row at the same fraction of its own per-knot budget: a 1 % pass
+    calibrates the fraction that fills the time budget."""
+    threads = os.cpu_count() or 1
+
+    def sweep(frac):
+        steps = secs = 0.0
+        for w in ws:
+            s_, t_, _ = oracle_sample(w, threads, threads, frac)
+            steps, secs = steps + s_, secs + t_
+        return steps, secs
+
+    _, secs = sweep(0.01)
+    frac = float(min(1.0, max(0.01, 0.01 * budget_s / max(secs, 1e-9))))
+    steps, secs = sweep(frac)
+    return {"value": steps / secs, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{threads} evenly spaced rows of each of the {len(ws)} problems, each at "
+                      f"{100 * frac:.1f} % of its per-knot budget ({steps:.3e} path-steps in "
+                      f"{secs:.1f} s, FP64, {threads} threads)"}
 
 
 def run_reference(args):
@@ -254,8 +287,12 @@ def run_gpu(args):
         launch = pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed)  # before warm-up, untimed
     pdds.pdds_set_timing(P.ctx, True)
 
-    def step():
+    def step(asm_ev=None):
+        if asm_ev:
+            asm_ev[0].record(stream)
         P.assemble(stream)
+        if asm_ev:
+            asm_ev[1].record(stream)
         st = pdds.pdds_stats(P.ctx)
         P.solve(rtol=1e-12, maxit=5000, stream=stream)
         st2 = pdds.pdds_stats(P.ctx)
@@ -268,13 +305,16 @@ def run_gpu(args):
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # the whole pdds_assemble call (CSR/b clearing, unit prefix, path kernel, finalize)
+    asm_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
     path_ms, steps_done, launches, errors, iters = [], 0, 0, 0, []
     with Clocks(local) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()                    # evict L2 between timed steps
             ev[i][0].record(stream)
-            st, st2 = step()
+            st, st2 = step(asm_ev[i])
             ev[i][1].record(stream)
             path_ms.append(st["path_kernel_ms"])
             steps_done += st["path_steps"]
@@ -283,6 +323,7 @@ def run_gpu(args):
             iters.append(st2["solve_iters"])
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    asm_ms = [a.elapsed_time(b) for a, b in asm_ev]
     total_ms = sum(step_ms)
     total_ms_max, steps_all = reduce_timing(total_ms, float(steps_done), device="cuda")
     value = steps_all / (total_ms_max * 1e-3)
@@ -338,6 +379,9 @@ def run_gpu(args):
         "config": {"workload": w.name, "knots": n, "paths_per_knot": w.n_paths, "dt": w.dt,
                    "path_steps_per_step": steps_done / args.steps,
                    "assembly_ms": float(np.mean(path_ms)),
+                   "assemble_call_ms": {"median": float(np.median(asm_ms)),
+                                        "min": float(np.min(asm_ms)),
+                                        "reps": len(asm_ms)},
                    "solve_iters": int(np.median(iters)), "interface_rms_error": rms,
                    "accumulation": "f64", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -345,7 +389,7 @@ def run_gpu(args):
                               "exit_batch": launch[3],
                               "chosen_by": "default" if args.no_autotune else "pdds_autotune"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(w.name),
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.config),
                      "kernel": "path_kernel", "flops_per_path_step": fpk,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                     f"({src} max SM clock)"},
@@ -449,6 +493,7 @@ def run_batch(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "path_kernel",
                          "flops_per_path_step": FLOPS_PER_STEP[ws[0].coef_id]},
+            "cpu_baseline": None if args.no_baseline else cpu_baseline_batch(ws),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
@@ -470,6 +515,7 @@ def run_cv_study(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "knots": res["knots"], "dt": w.dt,
                        "paths_per_knot": n_plain},
+            "cpu_baseline": None if args.no_baseline else cpu_baseline(w),
             "cv_study": res}
     print(json.dumps(line), flush=True)
     return 0

@@ -143,9 +143,15 @@ class Problem:
         for i, v in enumerate(params):
             self.coef.params[i] = float(v)
         self._keep = []
+        if (sigma_tab is None) != (c_tab is None):
+            raise ValueError("oracle: sigma_tab and c_tab come together")
+        if int(coef_id) == COEF_TABLE and sigma_tab is None:
+            raise ValueError("oracle: the tabulated coefficient set needs sigma_tab and c_tab")
         if sigma_tab is not None:
             st = np.ascontiguousarray(sigma_tab, dtype=np.float32)
             ct = np.ascontiguousarray(c_tab, dtype=np.float32)
+            if st.ndim != 2 or st.shape != ct.shape or min(st.shape) < 2:
+                raise ValueError("oracle: tables must be two [ny][nx] arrays, nx, ny >= 2")
             self._keep += [st, ct]
             self.coef.tab_ny, self.coef.tab_nx = st.shape
             self.coef.sigma_tab = st.ctypes.data

@@ -913,6 +913,10 @@ static void* worker(void* arg) {
 static int job_begin(job_t* J, geom_t* G, const orc_grid* g, const orc_coeffs* cf,
                      const orc_run* run, const int32_t* rows, int32_t nrows) {
   if (!(run->dt > 0) || run->k_max < 1) return -1;
+  /* the tabulated set reads both tables at every step */
+  if (cf->id == ORC_COEF_TABLE &&
+      (!cf->sigma_tab || !cf->c_tab || cf->tab_nx < 2 || cf->tab_ny < 2))
+    return -1;
   if (geom_build(g, G, 1)) return -1;
   for (int r = 0; r < nrows; ++r)
     if (rows[r] < 0 || rows[r] >= G->n) { geom_free(G); return -2; }

@@ -89,6 +89,20 @@ def test_row_sums_equal_b_tabulated(orc):
     assert np.abs(P.dense(val) @ np.ones(P.n) - b).max() < 1e-12
 
 
+def test_tabulated_set_requires_tables(orc):
+    """The tabulated coefficient set reads both tables at every step: the
+    wrapper refuses to build it without them (or with mismatched shapes)
+    instead of handing the C code NULL tables."""
+    sig = np.full((5, 5), SQ2, dtype=np.float32)
+    with pytest.raises(ValueError):
+        orc.Problem(grid(2, 4, ext=2), orc.COEF_TABLE, params=(0.0, 1.0))
+    with pytest.raises(ValueError):
+        orc.Problem(grid(2, 4, ext=2), orc.COEF_TABLE, params=(0.0, 1.0), sigma_tab=sig)
+    with pytest.raises(ValueError):
+        orc.Problem(grid(2, 4, ext=2), orc.COEF_TABLE, params=(0.0, 1.0), sigma_tab=sig,
+                    c_tab=np.zeros((5, 4), dtype=np.float32))
+
+
 def test_time_space_scaling_is_exact(orc):
     """Eq. 26: E[tau] scales as Lambda^2.  With Lambda = 2, h' = 4h and the same
     random numbers the discrete paths are exact copies scaled by 2, so b' = 4 b
