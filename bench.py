@@ -198,7 +198,7 @@ def cpu_baseline(w, budget_s: float = 15.0):
     rate = steps / secs
     per_row = steps / len(rows)
     want = int(max(threads, min(w.extra.get("n_rows", 10**9), budget_s * rate / per_row)))
-    want = min(want, 400)
+    want = min(want, 4000)
     steps, secs, rows = oracle_sample(w, want, threads)
     return {"value": steps / secs, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(rows)} evenly spaced rows of {w.name} at N={w.n_paths}, "
