@@ -250,6 +250,54 @@ def test_batch_one_launch_matches_oracle(orc):
             assert abs(gb[k] - b[k]) < 12.0 / Nk[k] + 1e-9, (i, k)
 
 
+def test_config3_full_batch_sampled_rows(orc):
+    """All 16 config-3 problems at their full per-knot budgets in one batched
+    launch, as the benchmark runs them.  Problem 0 (Philox tag 0): its sampled
+    rows equal, to FP64 summation order, a single-problem launch with records
+    in which only those rows get paths (a path's counters depend on its step,
+    index, knot and tag only), and that launch goes against the oracle with
+    flagged paths removed.  Four small-patch problems (tags 3, 6, 13, 14):
+    sampled rows against the oracle within four flipped paths per row."""
+    ws = W.config3()
+    probs = [pdds.Problem(w) for w in ws]
+    pdds.pdds_assemble_batch([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs],
+                             0, [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
+    torch.cuda.synchronize()
+    assert pdds.pdds_stats(probs[0].ctx)["device_error"] == 0
+    # problem 0: batch == masked single launch (records) == oracle
+    w0, P0 = ws[0], probs[0]
+    Nk0 = P0.n_per_knot.cpu().numpy()
+    order = np.argsort(Nk0, kind="stable")
+    rows0 = np.sort(np.concatenate([order[:7], order[-1:]])).astype(np.int32)
+    mask = np.zeros_like(Nk0)
+    mask[rows0] = Nk0[rows0]
+    g = run_gpu(w0, records=True, n_per_knot=mask)
+    bv, bb = P0.val.cpu().numpy(), P0.b.cpu().numpy()
+    for k in rows0:
+        s_, e_ = g["row_ptr"][k], g["row_ptr"][k + 1]
+        assert np.allclose(bv[s_:e_], g["val"][s_:e_], rtol=1e-11, atol=1e-14), k
+        assert np.isclose(bb[k], g["b"][k], rtol=1e-11, atol=1e-14), k
+    o = run_oracle(orc, w0, rows=rows0, n_per_knot=Nk0)
+    g_rows = dict(g)
+    g_rows["rec"] = gpu_rows_records(g, rows0, mask)
+    parity.compare_rows(g_rows, o, rows0, Nk0[rows0], len(Nk0))
+    # other problems, their own tags
+    for i in (3, 6, 13, 14):
+        w, P = ws[i], probs[i]
+        Nk = P.n_per_knot.cpu().numpy()
+        order = np.argsort(Nk, kind="stable")
+        rows = np.sort(np.concatenate([order[:2], order[-1:]])).astype(np.int32)
+        O = orc.Problem(w.grid, w.coef_id, w.params)
+        val, b, _, _ = O.assemble(Nk, w.dt, w.seed, w.k_max, rows=rows, tag=i)
+        gv, gb = P.val.cpu().numpy(), P.b.cpu().numpy()
+        for k in rows:
+            s_, e_ = O.row_ptr[k], O.row_ptr[k + 1]
+            assert np.abs(gv[s_:e_] - val[s_:e_]).max() < 4.0 / Nk[k] + 1e-9, (i, k)
+            assert abs(gb[k] - b[k]) < 12.0 / Nk[k] + 1e-9, (i, k)
+    for P in probs:
+        P.close()
+
+
 def test_batch_replay_is_deterministic_in_structure():
     """Replaying the captured graph gives the same sums (to FP64 order)."""
     ws = W.config3()[3:5]
