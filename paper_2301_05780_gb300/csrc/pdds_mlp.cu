@@ -38,10 +38,18 @@ constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 43
 //             dh1[p][u] = sum_o g2[p][o] W2[o][u]
 // with h1 and g2 = dL/da2 staged in shared memory (rows padded to 68 floats:
 // the two row groups a warp reads fall in different banks).  The CTA's
-// partial gradient is added to grad with FP32 reductions; the CTA that
-// arrives last (a counter, nothing waits) then reads the complete gradient
-// and applies Adam, and clears the gradient and counter for the next launch.
-// The step index lives on the device, so identical launches can be queued.
+// partial gradient is added to grad with FP32 reductions.
+//
+// Training: launch t first applies the Adam update t (Kingma & Ba 2015) to
+// the previous launch's parameters with the previous launch's gradient --
+// every CTA computes it into its own shared-memory image of theta, CTA 0
+// writes theta, m and v back -- then takes the gradient at the new theta.
+// Gradients rotate through three buffers (accumulated in launch t, read in
+// t + 1, cleared by CTA 0 in t + 2 for t + 3), theta, m and v through two,
+// so no launch reads what it writes and nothing waits on other CTAs.  The
+// CTA that arrives last (a counter) advances the step index and the powers
+// beta^t; launch `steps` applies the last update only.  The step index lives
+// on the device, so identical launches can be queued.
 constexpr int kTrainThreads = 256;
 constexpr int kTileP = 64;
 constexpr int kLd = 68;
@@ -54,7 +62,6 @@ struct TrainSmem {
   float b3;
   float red_b3[16];
   double red_loss[16];
-  int last;
 };
 constexpr size_t kTrainSmemBytes = sizeof(TrainSmem);
 // the end-of-CTA column sums [5][16][64] are staged over h1 and g2 (adjacent)
@@ -65,25 +72,46 @@ static_assert(5 * 16 * 64 <= 2 * kTileP * kLd, "column-sum staging fits in h1 an
 // Step state of a training run (device, zeroed before the first step).
 struct TrainState {
   unsigned count;  // CTAs done with the current launch
-  int t;           // Adam steps completed
-  double p1, p2;   // beta1^t, beta2^t (read from step 2 on)
+  int t;           // index of the next launch
+  double p1, p2;   // beta1^t, beta2^t for launch t >= 1
 };
 
 struct TrainArgs {
-  float* theta;
+  float* theta;     // parameters (training: read by launch 0, written by the last)
   const float* xy;
   const float* tgt;
   int64_t npts;
   float scale;      // 2 / N: d loss / d v
   double inv_n;     // 1 / N
-  float* grad;      // accumulated gradient (zero on entry)
-  double* loss;     // loss accumulator; training: loss history, indexed by the step
+  float* grad;      // gradient: one buffer (gradient only) or three (training)
+  double* loss;     // loss; training: the loss history, indexed by the step
   // training only
-  float *m, *v;
+  float *th2, *m2, *v2;  // [2][kMlpParams] each
   TrainState* st;
   int steps;
   float lr, beta1, beta2, eps;
 };
+
+// Parameter i of theta (layout W1[64][2], b1, W2[64][64], b2, w3, b3) into
+// the shared-memory image.
+__device__ __forceinline__ void stage_param(TrainSmem& S, int i, float w) {
+  if (i < kOffB1) {
+    if (i & 1) S.w1y[i >> 1] = w;
+    else S.w1x[i >> 1] = w;
+  } else if (i < kOffW2) {
+    S.b1[i - kOffB1] = w;
+  } else if (i < kOffB2) {
+    const int j = i - kOffW2;
+    S.W2r[j >> 6][j & 63] = w;
+    S.W2c[j & 63][j >> 6] = w;
+  } else if (i < kOffW3) {
+    S.b2[i - kOffB2] = w;
+  } else if (i < kOffB3) {
+    S.w3[i - kOffW3] = w;
+  } else {
+    S.b3 = w;
+  }
+}
 
 __device__ __forceinline__ float logistic(float a) { return 1.0f / (1.0f + __expf(-a)); }
 
@@ -92,34 +120,70 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
   extern __shared__ __align__(16) unsigned char train_smem[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_smem);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  constexpr int kPer = (kMlpParams + kTrainThreads - 1) / kTrainThreads;
   int t = 0;
   if constexpr (ADAM) {
     t = __ldcg(&A.st->t);
-    if (t >= A.steps) return;  // a launch queued past the last step
+    if (t > A.steps) return;  // a launch queued past the last one
   }
-  const float* th = A.theta;
-  {
-    // all 16 loads of a thread in flight at once (one L2 round trip)
-    constexpr int kPer = kMlpHidden * kMlpHidden / kTrainThreads;
+  const bool grad_pass = !ADAM || t < A.steps;
+  if (!ADAM || t == 0) {
+    // theta as given; launch 0 of a training run also keeps a copy
     float w[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) w[q] = th[kOffW2 + tid + q * kTrainThreads];
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int i = tid + q * kTrainThreads;
-      S.W2r[i >> 6][i & 63] = w[q];
-      S.W2c[i & 63][i >> 6] = w[q];
+      w[q] = i < kMlpParams ? A.theta[i] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      if (i < kMlpParams) {
+        stage_param(S, i, w[q]);
+        if (ADAM && blockIdx.x == 0) A.th2[i] = w[q];
+      }
+    }
+  } else if (grad_pass || blockIdx.x == 0) {
+    // Adam update t from the parameters, moments and gradient of launch t - 1
+    const int rd = ((t - 1) & 1) * kMlpParams, wr = (t & 1) * kMlpParams;
+    const float* gp = A.grad + ((t - 1) % 3) * kMlpParams;
+    const float c1 = (float)(1.0 - __ldcg(&A.st->p1)), c2 = (float)(1.0 - __ldcg(&A.st->p2));
+    float g[kPer], mo[kPer], vo[kPer], to[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      if (i < kMlpParams) {
+        g[q] = __ldcg(gp + i);
+        mo[q] = __ldcg(A.m2 + rd + i);
+        vo[q] = __ldcg(A.v2 + rd + i);
+        to[q] = __ldcg(A.th2 + rd + i);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid + q * kTrainThreads;
+      if (i < kMlpParams) {
+        const float mi = A.beta1 * mo[q] + (1.f - A.beta1) * g[q];
+        const float vi = A.beta2 * vo[q] + (1.f - A.beta2) * g[q] * g[q];
+        const float th = to[q] - A.lr * (mi / c1) / (sqrtf(vi / c2) + A.eps);
+        stage_param(S, i, th);
+        if (blockIdx.x == 0) {
+          A.th2[wr + i] = th;
+          A.m2[wr + i] = mi;
+          A.v2[wr + i] = vi;
+          if (!grad_pass) A.theta[i] = th;  // the last update: the result
+        }
+      }
     }
   }
-  if (tid < kMlpHidden) {
-    S.w1x[tid] = th[kOffW1 + 2 * tid];
-    S.w1y[tid] = th[kOffW1 + 2 * tid + 1];
-    S.b1[tid] = th[kOffB1 + tid];
-    S.b2[tid] = th[kOffB2 + tid];
-    S.w3[tid] = th[kOffW3 + tid];
+  if (ADAM && blockIdx.x == 0) {
+    // clear the gradient buffer launch t + 1 accumulates into (last read by t - 1)
+    float* gz = A.grad + ((t + 1) % 3) * kMlpParams;
+    for (int i = tid; i < kMlpParams; i += kTrainThreads) gz[i] = 0.f;
   }
-  if (tid == 0) S.b3 = th[kOffB3];
   __syncthreads();
+  if (grad_pass) {
+  float* gacc = A.grad + (ADAM ? (t % 3) * kMlpParams : 0);
   const int c0 = 4 * tx, r0 = 4 * ty;
   float dW2[4][4] = {};                          // o = r0 + i, u = c0 + j
   float gw1x[4] = {}, gw1y[4] = {}, gb1[4] = {};  // u = c0 + j
@@ -258,7 +322,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) atomicAdd(A.grad + kOffW2 + (r0 + i) * kMlpHidden + c0 + j, dW2[i][j]);
+    for (int j = 0; j < 4; ++j) atomicAdd(gacc + kOffW2 + (r0 + i) * kMlpHidden + c0 + j, dW2[i][j]);
   // column sums over the 16 row groups (staged in the h1 array)
   float* red = &S.H1[0][0];  // [5][16][64] over h1 and g2
 #pragma unroll
@@ -281,57 +345,25 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
     for (int r = 0; r < 16; ++r) sum += red[(q * 16 + r) * 64 + c];
     const int off = q == 0 ? kOffW1 + 2 * c : q == 1 ? kOffW1 + 2 * c + 1
                   : q == 2 ? kOffB1 + c : q == 3 ? kOffB2 + c : kOffW3 + c;
-    atomicAdd(A.grad + off, sum);
+    atomicAdd(gacc + off, sum);
   }
   if (tid == 0) {
     float b = 0.f;
     double l = 0.0;
     for (int r = 0; r < 16; ++r) { b += S.red_b3[r]; l += S.red_loss[r]; }
-    atomicAdd(A.grad + kOffB3, b);
+    atomicAdd(gacc + kOffB3, b);
     atomicAdd(A.loss + t, l * A.inv_n);
   }
+  }
   if constexpr (ADAM) {
-    // Last CTA: Adam (Kingma & Ba 2015) with bias corrections 1 - beta^(t+1).
-    __threadfence();  // this thread's reductions before the arrival count
-    __syncthreads();
-    if (tid == 0) S.last = atomicAdd(&A.st->count, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!S.last) return;
-    __threadfence();
-    const double p1 = (t ? __ldcg(&A.st->p1) : 1.0) * (double)A.beta1;  // beta^(t+1)
-    const double p2 = (t ? __ldcg(&A.st->p2) : 1.0) * (double)A.beta2;
-    const float c1 = (float)(1.0 - p1), c2 = (float)(1.0 - p2);
-    // every load of a thread issued before the first update (one round trip)
-    constexpr int kPer = (kMlpParams + kTrainThreads - 1) / kTrainThreads;
-    float g[kPer], mo[kPer], vo[kPer], to[kPer];
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = tid + q * kTrainThreads;
-      if (i < kMlpParams) {
-        g[q] = __ldcg(A.grad + i);
-        mo[q] = A.m[i];
-        vo[q] = A.v[i];
-        to[q] = A.theta[i];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int i = tid + q * kTrainThreads;
-      if (i < kMlpParams) {
-        const float mi = A.beta1 * mo[q] + (1.f - A.beta1) * g[q];
-        const float vi = A.beta2 * vo[q] + (1.f - A.beta2) * g[q] * g[q];
-        A.grad[i] = 0.f;
-        A.m[i] = mi;
-        A.v[i] = vi;
-        A.theta[i] = to[q] - A.lr * (mi / c1) / (sqrtf(vi / c2) + A.eps);
-      }
-    }
-    __syncthreads();  // every thread has read the state
-    if (tid == 0) {
+    // the last CTA to arrive advances the step: every CTA read t and the
+    // powers before its arrival, and nothing else in this launch depends on
+    // what the last one writes
+    if (tid == 0 && atomicAdd(&A.st->count, 1u) == gridDim.x - 1) {
       A.st->count = 0;
+      A.st->p1 = (t == 0 ? 1.0 : A.st->p1) * (double)A.beta1;
+      A.st->p2 = (t == 0 ? 1.0 : A.st->p2) * (double)A.beta2;
       A.st->t = t + 1;
-      A.st->p1 = p1;
-      A.st->p2 = p2;
     }
   }
 }
@@ -475,8 +507,9 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
   cudaStream_t s = (cudaStream_t)cuda_stream;
   unsigned grid = 0;
   MCK(train_grid(npts, &grid));
-  // scratch: grad, m, v (FP32), the step state, the loss history
-  const size_t fbytes = 3 * kMlpParams * sizeof(float);
+  // scratch: three gradients and two each of theta, m, v (FP32), the step
+  // state, the loss history
+  const size_t fbytes = 9 * kMlpParams * sizeof(float);
   const size_t sbytes = (fbytes + 15) / 16 * 16;
   const size_t bytes = sbytes + sizeof(TrainState) + (size_t)steps * sizeof(double);
   char* buf = nullptr;
@@ -490,8 +523,9 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
   a.scale = 2.0f / (float)npts;
   a.inv_n = 1.0 / (double)npts;
   a.grad = f;
-  a.m = f + kMlpParams;
-  a.v = f + 2 * kMlpParams;
+  a.th2 = f + 3 * kMlpParams;
+  a.m2 = f + 5 * kMlpParams;
+  a.v2 = f + 7 * kMlpParams;
   a.st = reinterpret_cast<TrainState*>(buf + sbytes);
   a.loss = reinterpret_cast<double*>(buf + sbytes + sizeof(TrainState));
   a.steps = steps;
@@ -502,10 +536,10 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
   auto run = [&]() -> cudaError_t {
     cudaError_t r = cudaMemsetAsync(buf, 0, bytes, s);
     if (r != cudaSuccess) return r;
-    // The steps run as a CUDA graph of 64 identical launches replayed
-    // ceil(steps / 64) times on a private stream (the step index is read on
-    // the device; launches past the last step return at once): one graph
-    // launch per 64 steps instead of one kernel launch per step.
+    // steps + 1 launches (gradients 0..steps-1, updates 1..steps) run as a
+    // CUDA graph of 64 identical launches replayed on a private stream (the
+    // launch index is read on the device; launches past the last return at
+    // once): one graph launch per 64 kernel launches.
     cudaStream_t cs = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraph_t graph = nullptr;
@@ -516,7 +550,8 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
       if ((q = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return q;
       if ((q = cudaEventRecord(ev, s))) return q;
       if ((q = cudaStreamWaitEvent(cs, ev, 0))) return q;
-      const int chunk = std::min(steps, 64);
+      const int launches = steps + 1;
+      const int chunk = std::min(launches, 64);
       if ((q = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) return q;
       for (int k = 0; k < chunk; ++k)
         mlp_train_kernel<true><<<grid, kTrainThreads, kTrainSmemBytes, cs>>>(a);
@@ -525,7 +560,7 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
       if (lq) return lq;
       if (q) return q;
       if ((q = cudaGraphInstantiate(&exec, graph, 0))) return q;
-      for (int done = 0; done < steps; done += chunk)
+      for (int done = 0; done < launches; done += chunk)
         if ((q = cudaGraphLaunch(exec, cs))) return q;
       if ((q = cudaEventRecord(ev, cs))) return q;
       return cudaStreamWaitEvent(s, ev, 0);
