@@ -554,8 +554,8 @@ def run_e1(args):
     e3 = calibrated.error_summary(out["phase3"]["u"], ue, x["eps"])
     total_ms = [r["phase1"]["ms"] + r.get("fit", {}).get("ms", 0.0) + r["phase2"]["ms"] +
                 r["phase3"]["ms"] for r in runs]
-    steps = [r["phase1"]["path_steps"] + 2 * r["phase2"]["path_steps_gm_pass"] +
-             r["phase3"]["path_steps"] for r in runs]
+    steps = [r["phase1"]["path_steps"] + r["phase2"]["path_steps"] + r["phase3"]["path_steps"]
+             for r in runs]
     p2 = out["phase2"]
     line = {"metric": METRIC, "value": float(np.sum(steps) / (np.sum(total_ms) * 1e-3)),
             "unit": "path-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -565,12 +565,14 @@ def run_e1(args):
                        "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
                        "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
                        "control_variate": args.cv, "train_steps": args.train_steps,
-                       "note": "path-steps of the GM pass counted twice for the mixed run"},
+                       "note": "path-steps simulated in the three phases (the calibration's "
+                               "mixed GM/EM paths once, to their naive exits)"},
             "pipeline": {
                 "phase1": {"ms": out["phase1"]["ms"], "path_steps": out["phase1"]["path_steps"],
                            "errors": e1},
                 "fit_ms": out.get("fit", {}).get("ms"),
-                "phase2": {"ms": p2["ms"], "mean_bias_bound": p2["mean_bias_bound"],
+                "phase2": {"ms": p2["ms"], "path_steps": p2["path_steps"],
+                           "mean_bias_bound": p2["mean_bias_bound"],
                            "mean_predicted_vrf": p2["mean_predicted_vrf"],
                            "knots_with_h_below_h0": p2["knots_with_h_below_h0"],
                            "N_mean": float(np.mean(p2["N"])), "N_max": int(np.max(p2["N"])),

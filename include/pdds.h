@@ -260,8 +260,10 @@ pdds_status pdds_set_knot_steps(pdds_ctx* ctx, const double* h_per_knot);
  *                      sum xi, sum xi^2, sum phi_GM xi      (d = phi_EM - phi_GM)
  * in FP64 (DEVICE double[n][8]).  u0: DEVICE double[n]; n_per_knot / n_paths /
  * dt / seed as for pdds_assemble (per-knot steps apply when set).  The scheme
- * setting is ignored.  Allocates context-owned record scratch (40 bytes per
- * path and pass, kept for reuse) and synchronizes the stream. */
+ * setting is ignored.  One launch of the path kernel: each path records its
+ * GM exit and steps on to its naive exit, so the run costs the naive paths'
+ * steps.  Allocates context-owned record scratch (two 40-byte records per
+ * path, kept for reuse) and synchronizes the stream. */
 pdds_status pdds_calibrate(pdds_ctx* ctx, const double* u0, const int64_t* n_per_knot,
                            int64_t n_paths, double dt, uint64_t seed, double* moments,
                            void* cuda_stream);

@@ -129,7 +129,8 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     st2 = pdds.pdds_stats(P.ctx)
     d = diag.cpu().numpy()
     rho2 = d[:, 2]
-    out["phase2"] = {"ms": t2, "path_steps_gm_pass": st2["path_steps"],
+    # one mixed GM/EM pass: every step of every path simulated once
+    out["phase2"] = {"ms": t2, "path_steps": st2["path_steps"],
                      "h": h_i.cpu().numpy(), "N": N_i.cpu().numpy(), "gap": d[:, 0],
                      "var": d[:, 1], "rho2": rho2,
                      "mean_bias_bound": float(np.mean(np.abs(d[:, 0])) / 2),

@@ -701,6 +701,15 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
   uint32_t p = 0, kk = 0, tagw = 0;
   constexpr bool kPhiloxPre = EXT && CV == 0;  // the per-path Philox constants
   PhiloxPath ph{0u, 0u, 0u, 0u};
+  // Mixed GM/EM run of the calibration (Sec. 4.1; records kernels with the
+  // extended exit, P.mixed): a path first records its Gobet-Menozzi exit,
+  // then steps on inside the closed patch to its naive exit, which is
+  // accumulated and recorded like any other; it resumes at the step after
+  // its GM exit, with that step's Gaussian pair.  pend_em: the naive exit
+  // fell on the step of the Gobet-Menozzi one (or the path was truncated)
+  // and is resolved in the next round.
+  constexpr bool kMixed = EXT && RECORD;
+  bool gm_phase = false, pend_em = false, pend_tr = false;
   int n = 0;
   float xk = 0.f, yk = 0.f, bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
   float X = 0.f, Y = 0.f, Sx = 0.f, Z = 0.f, XI = 0.f;
@@ -758,6 +767,10 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           const float dm = gmc * sigma_bound<COEF>(H);
           bx0 += dm; bx1 -= dm; by0 += dm; by1 -= dm;
         }
+        if constexpr (kMixed) {
+          gm_phase = P.mixed != 0;
+          pend_em = pend_tr = false;
+        }
         n = 0; X = 0.f; Y = 0.f; Sx = 0.f; Z = 0.f; XI = 0.f;
       }
       if (base + cnt >= pend) ++want;     // unit fully handed out
@@ -785,6 +798,10 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
     // 32-bit step cap (the API keeps caps below 2^31): one compare per step
     const int kmax = (int)min(EXT ? kmax_l : P.kmax, (int64_t)0x7fffffff);
     bool exited = false, trunc = false;
+    if constexpr (kMixed) {
+      exited = alive && pend_em;
+      trunc = pend_tr;
+    }
     for (;;) {
       if constexpr (CV == 1) {
         // Same step as below, but the warp stays converged for the tensor-core
@@ -802,7 +819,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         for (int half = 0; half < 2; ++half) {
           float gx, gy, vv;
           mlp_grad_warp<false>(*mlp_s, xk + X, yk + Y, gx, gy, vv);
-          if (go && !exited) {
+          if (go && !exited && (!kMixed || half >= (n & 1))) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
             coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
@@ -837,7 +854,9 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         box_muller(r.z, r.w, z[2], z[3]);
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-          if (!exited) {
+          // a Philox call serves steps 2q and 2q + 1; a mixed-run path that
+          // resumes at an odd step takes the second half of its call
+          if (!exited && (!kMixed || half >= (n & 1))) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
             coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
@@ -883,6 +902,8 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
 
     // ---- resolve the exits (Eq. 22-25, corner rule of Sec. 3.3) -----------
     const bool leaving = alive && exited;
+    bool gm_rec = false;  // a Gobet-Menozzi exit of a mixed run: recorded, the path goes on
+    if constexpr (kMixed) gm_rec = leaving && gm_phase;
     double bc = 0.0;
     int side = 0, flags = 0;
     float Yk = 1.0f, sl = 0.f, s_line = 0.f;
@@ -968,7 +989,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
                                           fmaf((float)lj, H.dy, H.y0));
             } else {
               const int slot = kd.off[side] + t + q;
-              atomicAdd(acc + slot, qw[q]);
+              if (!gm_rec) atomicAdd(acc + slot, qw[q]);
               if constexpr (RECORD) {
                 const ProbDesc& D = prob_desc(P, H.prob);
                 const int c = D.slot2csr[kd.slot_base + slot];
@@ -994,6 +1015,8 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         const int r_side = __shfl_sync(kFull, side, src);
         const float r_s = __shfl_sync(kFull, sl, src);
         const float r_Y = __shfl_sync(kFull, Yk, src);
+        bool r_gm = false;
+        if constexpr (kMixed) r_gm = __shfl_sync(kFull, gm_rec ? 1 : 0, src) != 0;
         const Stage& H = S.st(r_st);
         const KnotDesc& kd = H.kd;
         const ProbDesc& D = prob_desc(P, H.prob);
@@ -1014,7 +1037,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             const int lj = vertical ? tl : kd.line[r_side];
             dsum += (double)w * (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
                                                       fmaf((float)lj, H.dy, H.y0));
-          } else {
+          } else if (!r_gm) {
             // signed weights in 2^-30 units (two's complement in the slot)
             atomicAdd(acc + kd.off[r_side] + j,
                       (unsigned long long)__float2ll_rn(w * kFixedOne));
@@ -1026,10 +1049,12 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
       }
     }
     if (leaving) {
-      my_steps += (unsigned long long)n;
-      my_paths += 1;
-      my_trunc += (flags & 1);
-      my_clamp += (flags >> 1) & 1;
+      if (!gm_rec) {
+        my_steps += (unsigned long long)n;
+        my_paths += 1;
+        my_trunc += (flags & 1);
+        my_clamp += (flags >> 1) & 1;
+      }
       if constexpr (RECORD) {
         const ProbDesc& D = prob_desc(P, S.st(st).prob);
         const int64_t idx = (D.path_prefix ? D.path_prefix[kk] : (int64_t)kk * D.n_paths) + p;
@@ -1037,14 +1062,27 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         R.steps = n; R.side_flags = side | (flags << 8); R.col_a = col_a; R.col_b = col_b;
         R.w_a = wa; R.w_b = wb; R.b_contrib = (float)bc; R.Y = Yk;
         R.xi = XI; R.s_line = s_line;
-        P.records[idx] = R;
+        (gm_rec ? P.records_gm : P.records)[idx] = R;
       }
-      atomicAdd(&S.st(st).bsum, bc);  // one FP64 shared atomic per exit
+      if (!gm_rec) atomicAdd(&S.st(st).bsum, bc);  // one FP64 shared atomic per exit
+    }
+    if constexpr (kMixed) {
+      if (gm_rec) {
+        // on to the naive exit: the closed patch, no shift
+        const KnotDesc& kd = S.st(st).kd;
+        gm_phase = false;
+        gmc = 0.f;
+        bx0 = kd.box[0]; bx1 = kd.box[1]; by0 = kd.box[2]; by1 = kd.box[3];
+        pend_tr = trunc;
+        pend_em = trunc || (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+      } else if (leaving) {
+        pend_em = pend_tr = false;
+      }
     }
     // warp-aggregated completion counts per stage
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const unsigned m = __ballot_sync(kFull, leaving && st == s);
+      const unsigned m = __ballot_sync(kFull, leaving && !gm_rec && st == s);
       if (m == 0) continue;
       __syncwarp();
       __threadfence_block();
@@ -1063,7 +1101,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         __syncwarp();
       }
     }
-    if (leaving) alive = false;
+    if (leaving && !gm_rec) alive = false;
   }
 
   // per-launch counters

@@ -385,7 +385,8 @@ int64_t default_kmax(const pdds_ctx* c, double dt) {
 pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, int nprob,
                       double dt, uint64_t seed, int64_t kmax, pdds::PathRecordDev* rec,
                       cudaStream_t stream, size_t sbytes, int max_slots, int tile_w, int tile_h,
-                      int coef_id, bool ext = false, bool gm = false) {
+                      int coef_id, bool ext = false, bool gm = false,
+                      pdds::PathRecordDev* rec_gm = nullptr) {
   pdds::KParams kp{};
   kp.prob0 = p0;
   kp.probs = d_probs;
@@ -410,7 +411,8 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   kp.tile_w = tile_w;
   kp.tile_h = tile_h;
   kp.stage_bytes = (int)sbytes;
-  kp.rec_mode = rec != nullptr;
+  kp.mixed = rec_gm != nullptr ? 1 : 0;
+  kp.records_gm = rec_gm;
   // a wait may outlast the slowest path of a unit: K_max steps at ~4 us
   // (per-knot steps: the longest cap is kmax dt / h_min steps)
   const double kmax_eff = ext && c->d_hknot && c->h_min < dt ? (double)kmax * dt / c->h_min
@@ -444,10 +446,12 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   return PDDS_OK;
 }
 
-// scheme: PDDS_SCHEME_EM / _GM, or -1 for the context's setting.
+// scheme: PDDS_SCHEME_EM / _GM, or -1 for the context's setting.  rec_gm
+// (with rec, GM scheme): the mixed GM/EM run, Gobet-Menozzi exits to rec_gm,
+// naive exits to rec and into G and b.
 pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, uint64_t seed,
                           pdds_csr* G, double* b, pdds_path_record* rec, cudaStream_t s,
-                          int scheme = -1) {
+                          int scheme = -1, pdds_path_record* rec_gm = nullptr) {
   (void)cudaGetLastError();  // a failed call elsewhere must not be reported here
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PDDS_EINVAL, "assemble: dt must be > 0");
   if (!N && (Nu < 1 || Nu >= ((int64_t)1 << 31)))
@@ -481,7 +485,8 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   const bool ext = gm || c->d_hknot != nullptr || c->interp == PDDS_INTERP_RBF;
   if (pdds_status e = run_paths(c, D, nullptr, 1, dt, seed, kmax,
                                 reinterpret_cast<pdds::PathRecordDev*>(rec), s, stage_bytes(c),
-                                c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id, ext, gm))
+                                c->geo.max_slots, c->tile_w, c->tile_h, c->coef_id, ext, gm,
+                                reinterpret_cast<pdds::PathRecordDev*>(rec_gm)))
     return e;
   ++launches;
   CK(c, pdds::launch_finalize(G->row_ptr, G->col, G->val, b, N, Nu, c->geo.n, s));
@@ -1020,22 +1025,19 @@ pdds_status pdds_calibrate(pdds_ctx* c, const double* u0, const int64_t* N, int6
   pdds_csr G{n, nnz, c->cal_rp, c->cal_col, c->cal_val};
   pdds_path_record* rec_em = c->cal_rec;
   pdds_path_record* rec_gm = c->cal_rec + c->cal_rec_cap;
-  // the same counters in both passes, so both passes follow the same paths: the
-  // GM pass stops at the first step beyond a moved side, the naive pass goes
-  // on to the first step outside the patch -- the mixed trajectory of Sec. 4.1
-  if (pdds_status e = assemble_impl(c, N, Nu, dt, seed, &G, c->cal_b, rec_em, s, PDDS_SCHEME_EM))
-    return e;
-  const int launches = c->st.kernel_launches;
-  const pdds_stats_t em_st = c->st;
-  if (pdds_status e = assemble_impl(c, N, Nu, dt, seed, &G, c->cal_b, rec_gm, s, PDDS_SCHEME_GM))
+  // One pass of the mixed trajectory of Sec. 4.1: each path records its first
+  // step beyond a moved side (GM), then steps on to its first step outside
+  // the patch (naive), which is recorded and accumulated -- the naive run's
+  // paths, the GM exits on the way.
+  if (pdds_status e = assemble_impl(c, N, Nu, dt, seed, &G, c->cal_b, rec_em, s,
+                                    PDDS_SCHEME_GM, rec_gm))
     return e;
   CK(c, pdds::launch_calib_moments(reinterpret_cast<const pdds::PathRecordDev*>(rec_em),
                                    reinterpret_cast<const pdds::PathRecordDev*>(rec_gm),
                                    N ? c->d_path_prefix : nullptr, Nu, u0, n, moments,
                                    make_prob(c, 0), s));
   CK(c, cudaStreamSynchronize(s));
-  c->st.kernel_launches += launches + 1;
-  c->st.path_kernel_ms += em_st.path_kernel_ms;
+  c->st.kernel_launches += 1;
   return PDDS_OK;
 }
 

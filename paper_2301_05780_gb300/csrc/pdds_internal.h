@@ -106,8 +106,9 @@ struct KParams {
   int32_t max_slots;       // accumulator slots per stage
   int32_t tile_w, tile_h;  // TABLE tile (nodes)
   int32_t stage_bytes;     // bytes per stage in dynamic shared memory
-  int32_t rec_mode;
+  int32_t mixed;           // records kernels with the extended exit: 1 = mixed GM/EM run
   int32_t pad_;
+  PathRecordDev* records_gm;  // mixed run: the Gobet-Menozzi exit of each path
   uint64_t wait_ns;        // bound on any device-side wait
   const void* mlp;         // staged control-variate network (MlpSmem), or nullptr
   int32_t unit_domain;     // every problem's Omega lies in [-1, 1]^2 (no trig reduction)
