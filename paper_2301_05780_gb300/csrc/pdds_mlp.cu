@@ -50,8 +50,9 @@ constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 43
 // CTA that arrives last (a counter) advances the step index and the powers
 // beta^t; launch `steps` applies the last update only.  The step index lives
 // on the device, so identical launches can be queued.
-constexpr int kTrainThreads = 256;
 constexpr int kTileP = 64;
+constexpr int kMR = 4;                              // rows of a thread's micro-tile
+constexpr int kTrainThreads = 16 * (kTileP / kMR);  // 16 column groups x kTileP / kMR row groups
 constexpr int kLd = 68;
 struct TrainSmem {
   float W2r[kMlpHidden][kLd];  // W2[o][u]
@@ -60,14 +61,15 @@ struct TrainSmem {
   float G2[kTileP][kLd];       // dL/da2     [p][o]
   float w1x[kMlpHidden], w1y[kMlpHidden], b1[kMlpHidden], b2[kMlpHidden], w3[kMlpHidden];
   float b3;
-  float red_b3[16];
-  double red_loss[16];
+  float red_b3[kTileP / kMR];
+  double red_loss[kTileP / kMR];
 };
 constexpr size_t kTrainSmemBytes = sizeof(TrainSmem);
 // the end-of-CTA column sums [5][16][64] are staged over h1 and g2 (adjacent)
 static_assert(offsetof(TrainSmem, G2) == offsetof(TrainSmem, H1) + sizeof(float) * kTileP * kLd,
               "g2 follows h1");
-static_assert(5 * 16 * 64 <= 2 * kTileP * kLd, "column-sum staging fits in h1 and g2");
+static_assert(5 * (kTrainThreads / 32) * 64 <= 2 * kTileP * kLd,
+              "column-sum staging fits in h1 and g2");
 
 // Step state of a training run (device, zeroed before the first step).
 struct TrainState {
@@ -184,8 +186,8 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
   __syncthreads();
   if (grad_pass) {
   float* gacc = A.grad + (ADAM ? (t % 3) * kMlpParams : 0);
-  const int c0 = 4 * tx, r0 = 4 * ty;
-  float dW2[4][4] = {};                          // o = r0 + i, u = c0 + j
+  const int c0 = 4 * tx, r0 = kMR * ty;
+  float dW2[kMR][4] = {};                          // o = r0 + i, u = c0 + j
   float gw1x[4] = {}, gw1y[4] = {}, gb1[4] = {};  // u = c0 + j
   float gb2[4] = {}, gw3[4] = {};                 // o = c0 + j
   float gb3 = 0.f;
@@ -193,17 +195,17 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
   const int64_t ntiles = (A.npts + kTileP - 1) / kTileP;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t p0 = tile * kTileP + r0;
-    float px[4], py[4], pt[4];
-    bool pv[4];
+    float px[kMR], py[kMR], pt[kMR];
+    bool pv[kMR];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kMR; ++i) {
       pv[i] = p0 + i < A.npts;
       px[i] = pv[i] ? A.xy[2 * (p0 + i)] : 0.f;
       py[i] = pv[i] ? A.xy[2 * (p0 + i) + 1] : 0.f;
       pt[i] = pv[i] ? A.tgt[p0 + i] : 0.f;
     }
     // h1 = SiLU(W1 x + b1) and SiLU'(a1) of this thread's (p, u) block
-    float d1[4][4];
+    float d1[kMR][4];
     {
       const float4 wx = *reinterpret_cast<const float4*>(&S.w1x[c0]);
       const float4 wy = *reinterpret_cast<const float4*>(&S.w1y[c0]);
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
       const float cwx[4] = {wx.x, wx.y, wx.z, wx.w}, cwy[4] = {wy.x, wy.y, wy.z, wy.w};
       const float cb[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < kMR; ++i) {
         float h[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -225,11 +227,11 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
     }
     __syncthreads();
     // forward: a2 = h1 W2^T + b2 (p = r0 + i, o = c0 + j)
-    float acc[4][4];
+    float acc[kMR][4];
     {
       const float4 bb = *reinterpret_cast<const float4*>(&S.b2[c0]);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < kMR; ++i) {
         acc[i][0] = bb.x; acc[i][1] = bb.y; acc[i][2] = bb.z; acc[i][3] = bb.w;
       }
     }
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
       const float4 w = *reinterpret_cast<const float4*>(&S.W2c[u][c0]);
       const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < kMR; ++i) {
         const float h = S.H1[r0 + i][u];
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(h, wv[j], acc[i][j]);
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
       const float cw3[4] = {w.x, w.y, w.z, w.w};
       const float b3 = S.b3;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < kMR; ++i) {
         float h2[4], sp[4], vp = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -283,31 +285,38 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
     // dW2[o][u] += sum_p g2[p][o] h1[p][u] (o = r0 + i, u = c0 + j)
 #pragma unroll 8
     for (int p = 0; p < kTileP; ++p) {
-      const float4 g = *reinterpret_cast<const float4*>(&S.G2[p][r0]);
+      float gv[kMR];
+      if constexpr (kMR == 4) {
+        const float4 g = *reinterpret_cast<const float4*>(&S.G2[p][r0]);
+        gv[0] = g.x; gv[1] = g.y; gv[2] = g.z; gv[3] = g.w;
+      } else {
+        const float2 g = *reinterpret_cast<const float2*>(&S.G2[p][r0]);
+        gv[0] = g.x; gv[1] = g.y;
+      }
       const float4 h = *reinterpret_cast<const float4*>(&S.H1[p][c0]);
-      const float gv[4] = {g.x, g.y, g.z, g.w}, hv[4] = {h.x, h.y, h.z, h.w};
+      const float hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < kMR; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) dW2[i][j] = fmaf(gv[i], hv[j], dW2[i][j]);
     }
     // dh1[p][u] = sum_o g2[p][o] W2[o][u] (p = r0 + i, u = c0 + j), then
     // da1 = dh1 SiLU'(a1) into the first layer's gradient
     {
-      float dh[4][4] = {};
+      float dh[kMR][4] = {};
 #pragma unroll 8
       for (int o = 0; o < kMlpHidden; ++o) {
         const float4 w = *reinterpret_cast<const float4*>(&S.W2r[o][c0]);
         const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kMR; ++i) {
           const float g = S.G2[r0 + i][o];
 #pragma unroll
           for (int j = 0; j < 4; ++j) dh[i][j] = fmaf(g, wv[j], dh[i][j]);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < kMR; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float da = dh[i][j] * d1[i][j];
@@ -320,18 +329,22 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
   }
   // ---- the CTA's partial gradient into grad
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < kMR; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) atomicAdd(gacc + kOffW2 + (r0 + i) * kMlpHidden + c0 + j, dW2[i][j]);
-  // column sums over the 16 row groups (staged in the h1 array)
-  float* red = &S.H1[0][0];  // [5][16][64] over h1 and g2
+  // column sums: the two row groups of a warp (lanes 0-15, 16-31) by a
+  // shuffle, then over the warps (staged over h1 and g2)
+  constexpr int kWarps = kTrainThreads / 32;
+  float* red = &S.H1[0][0];  // [5][kWarps][64]
+  const int wp = tid >> 5;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    red[(0 * 16 + ty) * 64 + c0 + j] = gw1x[j];
-    red[(1 * 16 + ty) * 64 + c0 + j] = gw1y[j];
-    red[(2 * 16 + ty) * 64 + c0 + j] = gb1[j];
-    red[(3 * 16 + ty) * 64 + c0 + j] = gb2[j];
-    red[(4 * 16 + ty) * 64 + c0 + j] = gw3[j];
+    const float v[5] = {gw1x[j], gw1y[j], gb1[j], gb2[j], gw3[j]};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float sum2 = v[q] + __shfl_xor_sync(0xffffffffu, v[q], 16);
+      if (!(tid & 16)) red[(q * kWarps + wp) * 64 + c0 + j] = sum2;
+    }
   }
   if (tx == 0) {
     S.red_b3[ty] = gb3;
@@ -342,7 +355,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
     const int q = e >> 6, c = e & 63;
     float sum = 0.f;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) sum += red[(q * 16 + r) * 64 + c];
+    for (int r = 0; r < kWarps; ++r) sum += red[(q * kWarps + r) * 64 + c];
     const int off = q == 0 ? kOffW1 + 2 * c : q == 1 ? kOffW1 + 2 * c + 1
                   : q == 2 ? kOffB1 + c : q == 3 ? kOffB2 + c : kOffW3 + c;
     atomicAdd(gacc + off, sum);
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(kTrainThreads, 2) mlp_train_kernel(const Train
   if (tid == 0) {
     float b = 0.f;
     double l = 0.0;
-    for (int r = 0; r < 16; ++r) { b += S.red_b3[r]; l += S.red_loss[r]; }
+    for (int r = 0; r < kTileP / kMR; ++r) { b += S.red_b3[r]; l += S.red_loss[r]; }
     atomicAdd(gacc + kOffB3, b);
     atomicAdd(A.loss + t, l * A.inv_n);
   }
