@@ -344,11 +344,13 @@ pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
 /* Tabulated control variate (Sec. 4.2: F = sigma^T grad u0 stored as an
  * interpolatory look-up table): grad_xy is a DEVICE (or host) float array
  * [ny][nx][2] of (du0/dx, du0/dy) at the nodes of an nx x ny grid spanning
- * Omega (corners included); it is copied into the context.  From then on the
- * path kernel adds xi = -sum_n Y_n s(X_n) g(X_n) . dW_n, g the bilinear
- * interpolation of the table (replaces an attached network; NULL detaches).
- * Per step it costs four table reads instead of the network's two 64 x 64
- * products.  Available for every coefficient set.  Synchronizes.
+ * Omega (corners included); the context keeps it cell by cell (the four
+ * corners of each cell together, 32 bytes, 4x the node table's size).  From
+ * then on the path kernel adds xi = -sum_n Y_n s(X_n) g(X_n) . dW_n, g the
+ * bilinear interpolation of the table (replaces an attached network; NULL
+ * detaches).  Per step it costs one 32-byte cell read instead of the
+ * network's two 64 x 64 products.  Available for every coefficient set.
+ * Synchronizes (the device).
  * Errors: EINVAL (nx, ny < 2 or nx ny > 2^28), ENOMEM, ECUDA. */
 pdds_status pdds_set_control_variate_grid(pdds_ctx* ctx, const float* grad_xy, int32_t nx,
                                           int32_t ny);

@@ -242,7 +242,7 @@ struct pdds_ctx {
   // control variate (staged network image) and whether it is on
   void* d_mlp = nullptr;
   int cv_mode = 0;               // 0 none, 1 in-path network, 2 tabulated gradient
-  float* d_cvtab = nullptr;      // [cv_ny][cv_nx][2] grad u0 (mode 2), owned
+  float* d_cvtab = nullptr;      // [cv_ny-1][cv_nx-1][8] cell corners of grad u0 (mode 2), owned
   int cv_nx = 0, cv_ny = 0;
   bool unit_domain_all = false;  // set by a batched launch: all its domains in [-1,1]^2
   // exit scheme and per-knot steps (extended-exit kernels)
@@ -884,13 +884,22 @@ pdds_status pdds_set_control_variate_grid(pdds_ctx* c, const float* grad_xy, int
     return fail(c, PDDS_EINVAL, "set_control_variate_grid: need 2 <= nx, ny and nx*ny <= 2^28");
   (void)cudaGetLastError();
   const size_t count = (size_t)nx * ny * 2;
-  if (c->cv_nx * c->cv_ny != nx * ny) {
+  const size_t cells = (size_t)(nx - 1) * (ny - 1) * 8;
+  if (c->cv_nx != nx || c->cv_ny != ny) {
     CK(c, cudaFree(c->d_cvtab));
     c->d_cvtab = nullptr;
-    if (dalloc(&c->d_cvtab, count) != cudaSuccess)
+    c->cv_nx = c->cv_ny = 0;
+    if (dalloc(&c->d_cvtab, cells) != cudaSuccess)
       return fail(c, PDDS_ENOMEM, "set_control_variate_grid: table allocation failed");
   }
-  CK(c, cudaMemcpy(c->d_cvtab, grad_xy, count * 4, cudaMemcpyDefault));
+  float* nodes = nullptr;
+  if (dalloc(&nodes, count) != cudaSuccess)
+    return fail(c, PDDS_ENOMEM, "set_control_variate_grid: node staging allocation failed");
+  cudaError_t e = cudaMemcpy(nodes, grad_xy, count * 4, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = pdds::launch_cv_cells(nodes, nx, ny, c->d_cvtab, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(nodes);
+  CK(c, e);
   c->cv_nx = nx;
   c->cv_ny = ny;
   c->cv_mode = 2;

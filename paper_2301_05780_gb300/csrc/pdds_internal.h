@@ -131,6 +131,7 @@ cudaError_t mlp_stage(const float* theta, void* image, cudaStream_t stream);
 cudaError_t launch_unit_prefix(const int64_t* n_per_knot, int64_t n, int64_t unit_paths,
                                int64_t* knot_unit_prefix, int64_t* path_prefix,
                                cudaStream_t stream);
+cudaError_t launch_cv_cells(const float* nodes, int nx, int ny, float* cells, cudaStream_t s);
 cudaError_t launch_prob_prefix_single(const ProbDesc& D, int64_t* out, cudaStream_t stream);
 cudaError_t launch_prob_prefix(const ProbDesc* probs, int nprob, int64_t* out, cudaStream_t stream);
 size_t stage_header_bytes();

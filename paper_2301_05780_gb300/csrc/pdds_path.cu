@@ -129,6 +129,26 @@ cudaError_t launch_prob_prefix(const ProbDesc* probs, int nprob, int64_t* out, c
   return cudaGetLastError();
 }
 
+__global__ void cv_cells_kernel(const float* __restrict__ nodes, int nx, int ny,
+                                float* __restrict__ cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ncell = (int64_t)(nx - 1) * (ny - 1);
+  if (c >= ncell) return;
+  const int i = (int)(c % (nx - 1)), j = (int)(c / (nx - 1));
+  const float2* n2 = reinterpret_cast<const float2*>(nodes);
+  const float2 a = n2[(int64_t)j * nx + i], b = n2[(int64_t)j * nx + i + 1];
+  const float2 d0 = n2[(int64_t)(j + 1) * nx + i], d1 = n2[(int64_t)(j + 1) * nx + i + 1];
+  float4* o = reinterpret_cast<float4*>(cells) + 2 * c;
+  o[0] = make_float4(a.x, b.x, d0.x, d1.x);
+  o[1] = make_float4(a.y, b.y, d0.y, d1.y);
+}
+
+cudaError_t launch_cv_cells(const float* nodes, int nx, int ny, float* cells, cudaStream_t s) {
+  const int64_t ncell = (int64_t)(nx - 1) * (ny - 1);
+  cv_cells_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(nodes, nx, ny, cells);
+  return cudaGetLastError();
+}
+
 size_t stage_header_bytes() { return (size_t)kStageHdr; }
 
 cudaError_t launch_finalize(const int32_t* row_ptr, const int32_t* col, double* val, double* b,
