@@ -71,7 +71,7 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
     instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
     cv_kind: "table" tabulates grad v_theta on a grid of half the knot spacing
-    (the paper's look-up table of Sec. 4.2, four reads per step) or "network"
+    (the paper's look-up table of Sec. 4.2, one cell read per step) or "network"
     evaluates v_theta in the path (two 64 x 64 products per step).
     Returns the nodal solutions of Phases I and III, the calibration (h_i,
     N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and

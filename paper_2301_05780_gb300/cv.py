@@ -124,7 +124,7 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 1000,
     n_cv = int(max(64, round(max(n0, 256) * (rms_probe / rms_plain) ** 2 * 1.1)))
     out["launch_cv"] = pdds.pdds_autotune(P.ctx, n_cv, w.dt, w.seed + 7)
     t_cv, u_cv, steps_cv, k_cv = _assemble_solve(P, n_cv, w.seed + 7)
-    # the same network as Sec. 4.2's look-up table: four table reads per step
+    # the same network as Sec. 4.2's look-up table: one table-cell read per step
     t_tab_build = _ms(lambda: tabulate_gradient(P.ctx, fit.theta, w.grid, P.dev))
     out["launch_cv_table"] = pdds.pdds_autotune(P.ctx, n_cv, w.dt, w.seed + 11)
     t_tab, u_tab, steps_tab, k_tab = _assemble_solve(P, n_cv, w.seed + 11)
