@@ -248,30 +248,36 @@ __device__ __forceinline__ float tanh_small(float q) {
 //   G = x^2/100^2 + y^2/50^2;  Lap tanh q = (1 - T^2)(Lap q - 2 T |grad q|^2),
 //   Lap q = -((3/25)^2 + (1/20)^2) q.
 struct E1Terms {
-  float r, sr, cr, q, T, sa, ca, sb, cb;
+  float sr, cr, q, T, sa, ca, sb, cb;
 };
-__device__ __forceinline__ E1Terms e1_terms(float x, float y) {
+// The terms of u at (x, y) given r.
+__device__ __forceinline__ E1Terms e1_terms(float x, float y, float r) {
   E1Terms t;
-  const float r2 = fmaf(x * x, 0.01f, fmaf(y * y, 0.02f, 1.0f));
-  t.r = sqrtf(r2);
   const float inv2pi = 0.15915494309189535f;
-  sincos_2pi(t.r * inv2pi, t.sr, t.cr);
+  sincos_2pi(r * inv2pi, t.sr, t.cr);
   sincos_2pi(fmaf(0.12f, x, 0.05f * y) * inv2pi, t.sa, t.ca);
   sincos_2pi(fmaf(0.05f, x, -0.12f * y) * inv2pi, t.sb, t.cb);
   t.q = t.sa + t.sb;
   t.T = tanh_small(t.q);
   return t;
 }
+__device__ __forceinline__ float e1_r2(float x, float y) {
+  return fmaf(x * x, 0.01f, fmaf(y * y, 0.02f, 1.0f));
+}
+// u (boundary data, once per exit): r by the correctly rounded square root.
 __device__ __forceinline__ float e1_u(float x, float y) {
-  const E1Terms t = e1_terms(x, y);
+  const E1Terms t = e1_terms(x, y, sqrtf(e1_r2(x, y)));
   return fmaf(t.sr + t.T, 0.333333343f, 3.0f);
 }
+// f = Lap u (every step): 1/r from the hardware reciprocal square root
+// (r^2 >= 1; a few ulp, far below the FP32 path rounding), r = r^2 / r.
 __device__ __forceinline__ float e1_lap(float x, float y) {
-  const E1Terms t = e1_terms(x, y);
-  const float G = fmaf(x * x, 1e-4f, y * y * 4e-4f);
-  const float ir = 1.0f / t.r;
-  const float lap_r = fmaf(0.03f, ir, -G * ir * ir * ir);
-  const float lap_sin = fmaf(t.cr, lap_r, -t.sr * G * ir * ir);
+  const float r2 = e1_r2(x, y);
+  const float ir = rsqrtf(r2);
+  const E1Terms t = e1_terms(x, y, r2 * ir);
+  const float Gi2 = fmaf(x * x, 1e-4f, y * y * 4e-4f) * (ir * ir);  // G / r^2
+  const float lap_r = ir * (0.03f - Gi2);                           // 0.03 / r - G / r^3
+  const float lap_sin = fmaf(t.cr, lap_r, -t.sr * Gi2);
   const float qx = fmaf(0.12f, t.ca, 0.05f * t.cb);
   const float qy = fmaf(0.05f, t.ca, -0.12f * t.cb);
   const float lap_q = -0.0169f * t.q;
