@@ -417,7 +417,7 @@ def main():
                     help="skip the CPU-oracle baseline and the end-to-end leg (profiling runs)")
     ap.add_argument("--cv", default="table", choices=["table", "network"],
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
-    ap.add_argument("--train-steps", type=int, default=3000,
+    ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
     ap.add_argument("--interp", default="linear", choices=["linear", "rbf"],
                     help="stencil interpolation of the e1 pipeline (Sec. 2.1 RBF or linear)")

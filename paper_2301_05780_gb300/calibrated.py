@@ -64,7 +64,7 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
 
 
 def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | None = None,
-        h0p: float | None = None, control_variate: bool = True, train_steps: int = 3000,
+        h0p: float | None = None, control_variate: bool = True, train_steps: int = 1500,
         lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
         rbf_shape: float = 0.0, cv_kind: str = "table") -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
