@@ -250,13 +250,20 @@ __device__ __forceinline__ float tanh_small(float q) {
 struct E1Terms {
   float sr, cr, q, T, sa, ca, sb, cb;
 };
-// The terms of u at (x, y) given r.
-__device__ __forceinline__ E1Terms e1_terms(float x, float y, float r) {
+// sin and cos of an angle a in radians: the hardware sine on a itself when
+// the host has bounded |a| to a few tens of radians (direct), else after an
+// exact reduction to [-1/2, 1/2] turn.
+__device__ __forceinline__ void sincos_rad(float a, bool direct, float& s, float& c) {
+  if (direct) __sincosf(a, &s, &c);
+  else sincos_2pi(a * 0.15915494309189535f, s, c);
+}
+// The terms of u at (x, y) given r.  direct: |x|, |y| <= 256, so every angle
+// is below 45 rad.
+__device__ __forceinline__ E1Terms e1_terms(float x, float y, float r, bool direct) {
   E1Terms t;
-  const float inv2pi = 0.15915494309189535f;
-  sincos_2pi(r * inv2pi, t.sr, t.cr);
-  sincos_2pi(fmaf(0.12f, x, 0.05f * y) * inv2pi, t.sa, t.ca);
-  sincos_2pi(fmaf(0.05f, x, -0.12f * y) * inv2pi, t.sb, t.cb);
+  sincos_rad(r, direct, t.sr, t.cr);
+  sincos_rad(fmaf(0.12f, x, 0.05f * y), direct, t.sa, t.ca);
+  sincos_rad(fmaf(0.05f, x, -0.12f * y), direct, t.sb, t.cb);
   t.q = t.sa + t.sb;
   t.T = tanh_small(t.q);
   return t;
@@ -266,15 +273,15 @@ __device__ __forceinline__ float e1_r2(float x, float y) {
 }
 // u (boundary data, once per exit): r by the correctly rounded square root.
 __device__ __forceinline__ float e1_u(float x, float y) {
-  const E1Terms t = e1_terms(x, y, sqrtf(e1_r2(x, y)));
+  const E1Terms t = e1_terms(x, y, sqrtf(e1_r2(x, y)), false);
   return fmaf(t.sr + t.T, 0.333333343f, 3.0f);
 }
 // f = Lap u (every step): 1/r from the hardware reciprocal square root
 // (r^2 >= 1; a few ulp, far below the FP32 path rounding), r = r^2 / r.
-__device__ __forceinline__ float e1_lap(float x, float y) {
+__device__ __forceinline__ float e1_lap(float x, float y, bool direct) {
   const float r2 = e1_r2(x, y);
   const float ir = rsqrtf(r2);
-  const E1Terms t = e1_terms(x, y, r2 * ir);
+  const E1Terms t = e1_terms(x, y, r2 * ir, direct);
   const float Gi2 = fmaf(x * x, 1e-4f, y * y * 4e-4f) * (ir * ir);  // G / r^2
   const float lap_r = ir * (0.03f - Gi2);                           // 0.03 / r - G / r^3
   const float lap_sin = fmaf(t.cr, lap_r, -t.sr * Gi2);
@@ -344,7 +351,7 @@ __device__ __forceinline__ float bilinear(const float* T, int w, float fx, float
 // point relative to the knot (used by the tabulated set).
 template <int COEF>
 __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const float* tc,
-                                       float x, float y, float xr, float yr, bool unit_domain,
+                                       float x, float y, float xr, float yr, bool trig_direct,
                                        float& s, float& dx, float& dy, float& c, float& f) {
   if constexpr (COEF == PDDS_COEF_LAPLACE_EXPSIN) {
     s = 1.41421356237309505f; dx = 0.f; dy = 0.f; c = 0.f; f = 0.f;
@@ -353,7 +360,7 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
     // d = (sin 2 pi y, cos 2 pi x), c = -(1 + x^2), f = Lap u + d.grad u + c u.
     float sx, cx, sy, cy;
     const float pi = 3.14159265358979324f;
-    if (unit_domain) {  // |x|, |y| <= 1: pi x is already within [-pi, pi]
+    if (trig_direct) {  // |x|, |y| <= 1 (set on the host): pi x is within [-pi, pi]
       __sincosf(pi * x, &sx, &cx);
       __sincosf(pi * y, &sy, &cy);
     } else {
@@ -389,7 +396,7 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
     dx = 0.f; dy = 0.f; f = H.params[0];
   } else if constexpr (COEF == PDDS_COEF_POISSON_E1) {
     s = 1.41421356237309505f; dx = 0.f; dy = 0.f; c = 0.f;
-    f = e1_lap(x, y);
+    f = e1_lap(x, y, trig_direct);
   } else {
     s = H.params[0]; dx = H.params[1]; dy = H.params[2]; c = H.params[3]; f = H.params[4];
   }
@@ -421,7 +428,7 @@ __device__ __forceinline__ float sigma_bound(const Stage& H) {
 template <int COEF>
 __device__ __forceinline__ void gm_shifts(const Stage& H, const float* tsig, const float* tc,
                                           float xk, float yk, float X, float Y, float gmc,
-                                          bool unit_domain, float sh[4]) {
+                                          bool trig_direct, float sh[4]) {
   if constexpr (const_sigma<COEF>()) {
     const float d = gmc * sigma_bound<COEF>(H);
     sh[0] = sh[1] = sh[2] = sh[3] = d;
@@ -432,7 +439,7 @@ __device__ __forceinline__ void gm_shifts(const Stage& H, const float* tsig, con
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
       float s, ddx, ddy, c, f;
-      coeffs<COEF>(H, tsig, tc, xk + px[o], yk + py[o], px[o], py[o], unit_domain, s, ddx, ddy,
+      coeffs<COEF>(H, tsig, tc, xk + px[o], yk + py[o], px[o], py[o], trig_direct, s, ddx, ddy,
                    c, f);
       sh[o] = gmc * fabsf(s);
     }
@@ -443,9 +450,9 @@ __device__ __forceinline__ void gm_shifts(const Stage& H, const float* tsig, con
 template <int COEF>
 __device__ __noinline__ bool gm_outside(const Stage& H, const float* tsig, const float* tc,
                                         float xk, float yk, float X, float Y, float gmc,
-                                        int unit_domain) {
+                                        int trig_direct) {
   float sh[4];
-  gm_shifts<COEF>(H, tsig, tc, xk, yk, X, Y, gmc, unit_domain != 0, sh);
+  gm_shifts<COEF>(H, tsig, tc, xk, yk, X, Y, gmc, trig_direct != 0, sh);
   const float* b = H.kd.box;
   return (X > b[1] - sh[0]) | (Y > b[3] - sh[1]) | (X < b[0] + sh[2]) | (Y < b[2] + sh[3]);
 }
@@ -831,7 +838,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           if (go && !exited && (!kMixed || half >= (n & 1))) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
-            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
+            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.trig_direct,
                          s, ddx, ddy, c, f);
             const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
             float Yw = 1.0f;
@@ -846,7 +853,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
             if constexpr (EXT && !const_sigma<COEF>()) {
               if (exited && gmc > 0.f) exited = gm_outside<COEF>(H, S.tile(st, 0), S.tile(st, 1),
-                                                              xk, yk, X, Y, gmc, P.unit_domain);
+                                                              xk, yk, X, Y, gmc, P.trig_direct);
             }
             if (!exited && n >= kmax) { exited = true; trunc = true; }
           }
@@ -868,7 +875,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           if (!exited && (!kMixed || half >= (n & 1))) {
             const Stage& H = S.st(st);
             float s, ddx, ddy, c, f;
-            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.unit_domain,
+            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.trig_direct,
                          s, ddx, ddy, c, f);
             float Yw = 1.0f;
             if constexpr (has_c<COEF>()) {
@@ -883,7 +890,10 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             if constexpr (CV == 2) {
               // dxi = -Y s grad u0 . dW with grad u0 from the table (Eq. 37, Sec. 4.2)
               float gx, gy;
-              cv_table_grad(prob_desc(P, H.prob), xk + X, yk + Y, gx, gy);
+              // a control variate never runs batched (pdds_assemble_batch refuses
+              // it), so the table is problem 0's, read from the launch constants:
+              // no per-step loads of the problem descriptor
+              cv_table_grad(P.prob0, xk + X, yk + Y, gx, gy);
               XI = fmaf(-Yw * ssh, fmaf(gx, z[2 * half], gy * z[2 * half + 1]), XI);
             }
             if constexpr (has_drift<COEF>()) {
@@ -897,7 +907,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
             if constexpr (EXT && !const_sigma<COEF>()) {
               if (exited && gmc > 0.f) exited = gm_outside<COEF>(H, S.tile(st, 0), S.tile(st, 1),
-                                                              xk, yk, X, Y, gmc, P.unit_domain);
+                                                              xk, yk, X, Y, gmc, P.trig_direct);
             }
             if (!exited && n >= kmax) { exited = true; trunc = true; }
           }
@@ -929,7 +939,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         // no shift, gives the lane's moved box, used above)
         if (gmc > 0.f) {
           float sh[4];
-          gm_shifts<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk, yk, X, Y, gmc, P.unit_domain,
+          gm_shifts<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk, yk, X, Y, gmc, P.trig_direct,
                           sh);
           const float* tb = kd.box;
           ov[0] = X - (tb[1] - sh[0]);

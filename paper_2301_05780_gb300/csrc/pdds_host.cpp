@@ -244,7 +244,7 @@ struct pdds_ctx {
   int cv_mode = 0;               // 0 none, 1 in-path network, 2 tabulated gradient
   float* d_cvtab = nullptr;      // [cv_ny-1][cv_nx-1][8] cell corners of grad u0 (mode 2), owned
   int cv_nx = 0, cv_ny = 0;
-  bool unit_domain_all = false;  // set by a batched launch: all its domains in [-1,1]^2
+  double dom_bound_all = 0.0;  // set by a batched launch: max |coordinate| of all its domains
   // exit scheme and per-knot steps (extended-exit kernels)
   int scheme = PDDS_SCHEME_EM;
   double* d_hknot = nullptr;  // owned copy of h_k, or nullptr
@@ -421,12 +421,15 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   const int cv = nprob == 1 ? c->cv_mode : 0;
   kp.mlp = cv == 1 ? c->d_mlp : nullptr;
   {
-    // all problems of the launch inside [-1, 1]^2 (problem 0 here, the batch
-    // caller checks the rest through c->unit_domain_all)
+    // the largest |coordinate| of the launch's domains (problem 0 here, the
+    // batch caller gives the bound over all of them) decides whether the
+    // coefficient set's angles may skip the reduction
     const pdds_grid& g = c->grid;
-    const bool u0 = std::fabs(g.x0) <= 1 && std::fabs(g.x1) <= 1 && std::fabs(g.y0) <= 1 &&
-                    std::fabs(g.y1) <= 1;
-    kp.unit_domain = (nprob == 1 ? u0 : c->unit_domain_all) ? 1 : 0;
+    const double b0 = std::max(std::max(std::fabs(g.x0), std::fabs(g.x1)),
+                               std::max(std::fabs(g.y0), std::fabs(g.y1)));
+    const double B = nprob == 1 ? b0 : c->dom_bound_all;
+    const double lim = coef_id == PDDS_COEF_POISSON_E1 ? 256.0 : 1.0;
+    kp.trig_direct = B <= lim ? 1 : 0;
   }
   // the network step is ~10x heavier: wait bounds scale with it
   if (cv == 1 && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
@@ -1176,12 +1179,12 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
   if (!(dt > 0)) return fail(c0, PDDS_EINVAL, "assemble_batch: dt must be > 0");
   int max_slots = 0, tw = 0, th = 0;
   int64_t kmax = 0;
-  bool unit_all = true;
+  double dom_bound = 0.0;  // max |coordinate| over the batch's domains
   for (int i = 0; i < count; ++i) {
     pdds_ctx* c = ctxs[i];
     if (!c) return fail(c0, PDDS_EINVAL, "assemble_batch: NULL context in the list");
-    unit_all = unit_all && std::fabs(c->grid.x0) <= 1 && std::fabs(c->grid.x1) <= 1 &&
-               std::fabs(c->grid.y0) <= 1 && std::fabs(c->grid.y1) <= 1;
+    dom_bound = std::max({dom_bound, std::fabs(c->grid.x0), std::fabs(c->grid.x1),
+                          std::fabs(c->grid.y0), std::fabs(c->grid.y1)});
     if (c->coef_id != c0->coef_id)
       return fail(c0, PDDS_EINVAL, "assemble_batch: all problems need the same coefficient set");
     if (c->device != c0->device)
@@ -1200,7 +1203,7 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
     th = std::max(th, c->tile_h);
     kmax = std::max(kmax, c->k_max > 0 ? c->k_max : default_kmax(c, dt));
   }
-  c0->unit_domain_all = unit_all;
+  c0->dom_bound_all = dom_bound;
   cudaStream_t s = (cudaStream_t)stream;
   // Graph key: everything the captured sequence depends on.
   std::vector<uint64_t> key = {(uint64_t)count, (uint64_t)Nu, (uint64_t)seed, (uint64_t)kmax,
