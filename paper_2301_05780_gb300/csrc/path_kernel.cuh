@@ -381,9 +381,15 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
     // s = sqrt2 (1 + 0.3 sin 2 pi x sin 2 pi y), c = -1, u = e^{x/4} cos(y/2),
     // f = (s^2/2)(1/16 - 1/4) u + c u.
     float s1, c1, s2, c2, sh, ch;
-    sincos_2pi(x, s1, c1);
-    sincos_2pi(y, s2, c2);
-    sincos_2pi(y * (0.5f / kTwoPi), sh, ch);
+    if (trig_direct) {  // |x|, |y| <= 7 (set on the host): angles below 45 rad
+      __sincosf(kTwoPi * x, &s1, &c1);
+      __sincosf(kTwoPi * y, &s2, &c2);
+      __sincosf(0.5f * y, &sh, &ch);
+    } else {
+      sincos_2pi(x, s1, c1);
+      sincos_2pi(y, s2, c2);
+      sincos_2pi(y * (0.5f / kTwoPi), sh, ch);
+    }
     s = 1.41421356237309505f * fmaf(0.3f * s1, s2, 1.0f);
     const float u = __expf(0.25f * x) * ch;
     dx = 0.f; dy = 0.f; c = -1.0f;

@@ -428,7 +428,9 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
     const double b0 = std::max(std::max(std::fabs(g.x0), std::fabs(g.x1)),
                                std::max(std::fabs(g.y0), std::fabs(g.y1)));
     const double B = nprob == 1 ? b0 : c->dom_bound_all;
-    const double lim = coef_id == PDDS_COEF_POISSON_E1 ? 256.0 : 1.0;
+    const double lim = coef_id == PDDS_COEF_POISSON_E1 ? 256.0
+                       : coef_id == PDDS_COEF_VARSIGMA   ? 7.0
+                                                          : 1.0;
     kp.trig_direct = B <= lim ? 1 : 0;
   }
   // the network step is ~10x heavier: wait bounds scale with it

@@ -112,8 +112,9 @@ struct KParams {
   uint64_t wait_ns;        // bound on any device-side wait
   const void* mlp;         // staged control-variate network (MlpSmem), or nullptr
   int32_t trig_direct;     // the coefficient set's angles are small enough for the hardware
-                           // sine without reduction: Omega within [-1, 1]^2 (manufactured)
-                           // or [-256, 256]^2 (the Poisson problem of Sec. 5.1)
+                           // sine without reduction: Omega within [-1, 1]^2 (manufactured),
+                           // [-7, 7]^2 (variable sigma) or [-256, 256]^2 (the Poisson
+                           // problem of Sec. 5.1)
   int32_t gm;              // extended kernels: 1 = Gobet-Menozzi shift of the sides
   double dt;               // extended kernels: step at which kmax counts
 };
