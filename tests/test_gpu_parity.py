@@ -118,6 +118,31 @@ def test_row_sums_equal_b_tabulated_gpu():
     assert np.abs(G @ np.ones(n) - g["b"]).max() < 1e-12
 
 
+# ------------------------------------- angles with and without reduction
+@pytest.mark.parametrize("coef,lo,hi,H,m,N,dt", [
+    (W.COEF_MANUFACTURED, 1.0, 2.0, 3, 8, 400, 1e-4),      # past [-1, 1]^2
+    (W.COEF_VARSIGMA, 0.0, 8.0, 4, 4, 200, 1e-3),          # past [-7, 7]^2
+    (W.COEF_POISSON_E1, -260.0, 260.0, 4, 4, 40, 2.0),     # past [-256, 256]^2
+])
+def test_coefficients_on_domains_needing_angle_reduction(orc, coef, lo, hi, H, m, N, dt):
+    """Domains beyond the bounds under which the kernel feeds its angles to the
+    hardware sine directly take the exact reduction to half a turn: every row
+    against the oracle (the other tests cover the direct path)."""
+    s_lo, s_hi = {W.COEF_VARSIGMA: (math.sqrt(2) * 0.7, math.sqrt(2) * 1.3)}.get(
+        coef, (math.sqrt(2), math.sqrt(2)))
+    grid = dict(x0=lo, x1=hi, y0=lo, y1=hi, Hx=H, Hy=H, m=m)
+    grid["ext"] = W.stencil_extension(grid, s_hi, dt)
+    w = W.Workload(f"trig_{coef}", grid, coef, n_paths=N, dt=dt, seed=31 + coef,
+                   k_max=W.step_cap(grid, s_lo, dt), sigma_bounds=(s_lo, s_hi))
+    g = run_gpu(w)
+    o = run_oracle(orc, w)
+    n = len(g["b"])
+    L = (hi - lo) / H
+    mean_steps = o["stats"][0] / (n * N)
+    atol = parity.fp32_path_atol(L, mean_steps, L / m)
+    parity.compare_rows(g, o, np.arange(n), np.full(n, N), n, atol_raw=atol)
+
+
 # ------------------------------------------------ tiny cases, path by path
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_tiny_path_by_path(orc, N):
