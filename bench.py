@@ -61,10 +61,10 @@ def kernel_source_hash() -> str:
 PROFILES = {"cfg2": "path_kernel_cfg2_ncu.txt", "cfg4": "path_kernel_cfg4_tabulated_ncu.txt"}
 
 
-def profiled_traffic(config: str):
-    """DRAM bytes per launch of the path kernel from the committed ncu summary
-    of this workload, if the summary was taken on the current kernel source;
-    else None."""
+def profiled_value(config: str, key: str):
+    """A `key: value` figure of the committed ncu summary of this workload's
+    path kernel, if the summary was taken on the current kernel source; else
+    None."""
     if config not in PROFILES:
         return None
     p = os.path.join(ROOT, "profiles", PROFILES[config])
@@ -72,10 +72,31 @@ def profiled_traffic(config: str):
         return None
     txt = open(p).read()
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
-    if not (m_hash and m_b) or m_hash.group(1) != kernel_source_hash():
+    m_v = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_v) or m_hash.group(1) != kernel_source_hash():
         return None
-    return float(m_b.group(1))
+    return float(m_v.group(1))
+
+
+def profiled_traffic(config: str):
+    """DRAM bytes per launch of the path kernel (committed ncu summary)."""
+    return profiled_value(config, "dram_bytes_per_full_launch")
+
+
+def issue_roofline(config: str, path_steps_per_s: float, sm_max_mhz: float):
+    """The path kernel is bound by instruction issue: warp instructions per
+    path-step from the committed ncu summary times the live path-step rate,
+    against 152 SMs x 4 schedulers x one warp instruction per cycle."""
+    wi = profiled_value(config, "warp_instructions_per_path_step")
+    if wi is None:
+        return None
+    peak = SMS_GB300 * 4 * sm_max_mhz * 1e6
+    achieved = path_steps_per_s * wi
+    return {"warp_instructions_per_path_step": wi, "achieved_warp_inst_per_s": achieved,
+            "peak_warp_inst_per_s": peak, "frac": achieved / peak,
+            "source": "instructions per path-step from the committed ncu summary of this kernel "
+                      "source; peak = 152 SMs x 4 schedulers x 1 warp instruction/cycle x max SM "
+                      "clock"}
 
 
 class Clocks:
@@ -200,6 +221,9 @@ def cpu_baseline(w, budget_s: float = 15.0):
     want = int(max(threads, min(w.extra.get("n_rows", 10**9), budget_s * rate / per_row)))
     want = min(want, 4000)
     steps, secs, rows = oracle_sample(w, want, threads)
+    if secs < 0.5 * budget_s and want < 4000:   # the calibration overestimated a row's cost
+        want = int(min(4000, want * budget_s / max(secs, 1e-3)))
+        steps, secs, rows = oracle_sample(w, want, threads)
     return {"value": steps / secs, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(rows)} evenly spaced rows of {w.name} at N={w.n_paths}, "
                       f"dt={w.dt:g} ({steps:.3e} path-steps in {secs:.1f} s, FP64, "
@@ -391,6 +415,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.config),
                      "kernel": "path_kernel", "flops_per_path_step": fpk,
+                     "issue": issue_roofline(args.config, steps_done / args.steps / kernel_s,
+                                             sm_max),
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                     f"({src} max SM clock)"},
         "cpu_baseline": cpu,
