@@ -825,7 +825,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
     st = assemble_impl(c, N, Nu, dt, seed, &G, b, nullptr, s);
     if (st == PDDS_OK) ms = std::min(ms, c->st.path_kernel_ms);
   };
-  // round 1: every shape once on the sample; round 2: the best twelve again
+  // first pass: every shape once on the sample; second pass: the best twelve again
   // (a few-millisecond timing is noisy at the 2-3 % that separates the best)
   std::vector<float> ms(shapes.size(), 1e30f);
   for (size_t i = 0; i < shapes.size() && st == PDDS_OK; ++i) time_shape(shapes[i], dN, 0, ms[i]);
