@@ -1098,8 +1098,10 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         gm_phase = false;
         gmc = 0.f;
         bx0 = kd.box[0]; bx1 = kd.box[1]; by0 = kd.box[2]; by1 = kd.box[3];
-        pend_tr = trunc;
-        pend_em = trunc || (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+        // a GM exit on the step cap, still inside the patch, is the naive
+        // path's truncation at that same step
+        pend_tr = trunc || n >= kmax;
+        pend_em = pend_tr || (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
       } else if (leaving) {
         pend_em = pend_tr = false;
       }

@@ -193,14 +193,17 @@ def _moments(pe, pg, x, idx, n):
     return np.stack([np.bincount(idx, weights=c, minlength=n) for c in cols], axis=1)
 
 
-@pytest.mark.parametrize("use_cv", [False, True])
-def test_calibration_moments_parity(orc, use_cv):
+@pytest.mark.parametrize("use_cv,k_cap", [(False, None), (True, None), (False, 60)])
+def test_calibration_moments_parity(orc, use_cv, k_cap):
     """pdds_calibrate against the oracle's mixed GM/EM run on the same streams
     and the same u0: flagged paths (step count or side differing in either
     exit) removed by each side; moments agree to the FP32 path rounding (and
     to 2 % of the xi terms with the BF16 network); the kernel's moments are
-    those of its own per-path records."""
+    those of its own per-path records.  k_cap: a step cap that truncates a
+    large share of the paths (both exits of a truncated path at the cap)."""
     w = _small_manufactured(500, H=3, m=8)
+    if k_cap:
+        w.k_max = k_cap
     n = pdds.pdds_geometry_host(w.grid)[0].shape[0]
     N = w.n_paths
     u0 = np.random.default_rng(12).normal(1.0, 0.5, n)
@@ -254,6 +257,11 @@ def test_calibration_moments_parity(orc, use_cv):
     assert not bad.any(), (np.argwhere(bad)[:5], Mg_k[bad][:5], Mo_k[bad][:5])
     if not use_cv:
         assert np.all(Mg[:, 5:] == 0.0)
+    if k_cap:
+        trunc = ((recs[EM]["side_flags"] >> 8) & 1).mean()
+        assert trunc > 0.2, trunc
+        assert np.array_equal((recs[GM]["side_flags"] >> 8) & 1 & (recs[GM]["steps"] == k_cap),
+                              (recs[GM]["side_flags"] >> 8) & 1)
 
 
 def test_calibration_ragged_budgets():
