@@ -193,22 +193,33 @@ def _moments(pe, pg, x, idx, n):
     return np.stack([np.bincount(idx, weights=c, minlength=n) for c in cols], axis=1)
 
 
-@pytest.mark.parametrize("use_cv,k_cap", [(False, None), (True, None), (False, 60)])
-def test_calibration_moments_parity(orc, use_cv, k_cap):
+@pytest.mark.parametrize("use_cv,k_cap,knot_steps", [
+    (False, None, False), (True, None, False), (False, 60, False), (False, None, True),
+    ("table", None, False)])
+def test_calibration_moments_parity(orc, use_cv, k_cap, knot_steps):
     """pdds_calibrate against the oracle's mixed GM/EM run on the same streams
     and the same u0: flagged paths (step count or side differing in either
     exit) removed by each side; moments agree to the FP32 path rounding (and
     to 2 % of the xi terms with the BF16 network); the kernel's moments are
     those of its own per-path records.  k_cap: a step cap that truncates a
-    large share of the paths (both exits of a truncated path at the cap)."""
+    large share of the paths (both exits of a truncated path at the cap);
+    knot_steps: per-knot steps (and caps); use_cv "table": the tabulated
+    control variate (exact grad u on a 33 x 33 grid)."""
     w = _small_manufactured(500, H=3, m=8)
     if k_cap:
         w.k_max = k_cap
     n = pdds.pdds_geometry_host(w.grid)[0].shape[0]
     N = w.n_paths
     u0 = np.random.default_rng(12).normal(1.0, 0.5, n)
-    theta = None
-    if use_cv:
+    h_k = np.random.default_rng(14).uniform(0.3, 1.0, n) * w.dt if knot_steps else None
+    theta, tab = None, None
+    if use_cv == "table":
+        g = np.linspace(0.0, 1.0, 33)
+        X, Y = np.meshgrid(g, g)  # [ny][nx]
+        tab = np.stack([np.pi * np.cos(np.pi * X) * np.cos(np.pi * Y) + Y,
+                        -np.pi * np.sin(np.pi * X) * np.sin(np.pi * Y) + X],
+                       axis=-1).astype(np.float32)
+    elif use_cv:
         th = torch.tensor(W.mlp_init(), dtype=torch.float32, device="cuda")
         rng = np.random.default_rng(13)
         xy = rng.uniform(0, 1, size=(4096, 2))
@@ -217,7 +228,9 @@ def test_calibration_moments_parity(orc, use_cv, k_cap):
                             torch.tensor(tgt, dtype=torch.float32, device="cuda"), steps=400)
         theta = th
     # GPU: calibration moments, plus the two record passes it is made of
-    P = _problem(w, EM, theta=theta)
+    P = _problem(w, EM, h_per_knot=h_k, theta=theta)
+    if tab is not None:
+        pdds.pdds_set_control_variate_grid(P.ctx, torch.tensor(tab, device="cuda"))
     mom = torch.empty(n, 8, dtype=torch.float64, device="cuda")
     u0d = torch.tensor(u0, dtype=torch.float64, device="cuda")
     pdds.pdds_calibrate(P.ctx, u0d, mom, N, None, w.dt, w.seed)
@@ -236,7 +249,9 @@ def test_calibration_moments_parity(orc, use_cv, k_cap):
     assert np.allclose(Mg, own, rtol=1e-9, atol=1e-9)
     # oracle
     O = oracle_problem(orc, w, theta)
-    Mo, _, ro = O.calibrate(u0, N, w.dt, w.seed, w.k_max, records=True)
+    if tab is not None:
+        O.set_cv_table(tab)
+    Mo, _, ro = O.calibrate(u0, N, w.dt, w.seed, w.k_max, records=True, h_per_knot=h_k)
     flag = ((recs[EM]["steps"] != ro["steps_em"]) |
             ((recs[EM]["side_flags"] & 0xFF) != ro["side_em"]) |
             (recs[GM]["steps"] != ro["steps_gm"]) |
