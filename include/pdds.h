@@ -338,7 +338,8 @@ pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, flo
  * path's b contribution (Eq. 37, left-point Ito sum), which leaves E[b]
  * unchanged and lowers its variance as v approaches u.  NULL detaches it.
  * Available for PDDS_COEF_LAPLACE_EXPSIN, _MANUFACTURED, _CONSTANT and
- * _POISSON_E1. */
+ * _POISSON_E1 (EINVAL otherwise, nothing changed); a staging error (ECUDA)
+ * leaves no control variate attached. */
 pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
 
 /* Tabulated control variate (Sec. 4.2: F = sigma^T grad u0 stored as an
@@ -350,7 +351,7 @@ pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
  * bilinear interpolation of the table (replaces an attached network; NULL
  * detaches).  Per step it costs one 32-byte cell read instead of the
  * network's two 64 x 64 products.  Available for every coefficient set.
- * Synchronizes (the device).
+ * Synchronizes (the device).  On an error no control variate is attached.
  * Errors: EINVAL (nx, ny < 2 or nx ny > 2^28), ENOMEM, ECUDA. */
 pdds_status pdds_set_control_variate_grid(pdds_ctx* ctx, const float* grad_xy, int32_t nx,
                                           int32_t ny);

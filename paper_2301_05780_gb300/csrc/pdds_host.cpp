@@ -871,6 +871,7 @@ pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
   if (!pdds::path_kernel_has_cv(c->coef_id))
     return fail(c, PDDS_EINVAL, "set_control_variate: not available for this coefficient set");
   (void)cudaGetLastError();
+  c->cv_mode = 0;  // detached until the new network is staged (a failure leaves none)
   if (!c->d_mlp) CK(c, cudaMalloc(&c->d_mlp, pdds::mlp_image_bytes()));
   CK(c, pdds::mlp_stage(theta, c->d_mlp, nullptr));
   CK(c, cudaDeviceSynchronize());
@@ -888,6 +889,7 @@ pdds_status pdds_set_control_variate_grid(pdds_ctx* c, const float* grad_xy, int
   if (nx < 2 || ny < 2 || (int64_t)nx * ny > ((int64_t)1 << 28))
     return fail(c, PDDS_EINVAL, "set_control_variate_grid: need 2 <= nx, ny and nx*ny <= 2^28");
   (void)cudaGetLastError();
+  c->cv_mode = 0;  // detached until the new table is built (a failure leaves none)
   const size_t count = (size_t)nx * ny * 2;
   const size_t cells = (size_t)(nx - 1) * (ny - 1) * 8;
   if (c->cv_nx != nx || c->cv_ny != ny) {
