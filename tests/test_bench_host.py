@@ -1,0 +1,52 @@
+"""Host logic of bench.py that decides what its JSON line reports: figures
+taken from the committed ncu summaries only when those were captured on the
+current kernel source, and the issue-slot roofline built from them."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_profile_figures_follow_the_kernel_source(tmp_path, monkeypatch):
+    """A summary whose kernel_source_sha256_16 matches the current sources
+    yields its figures; a stale one (or a missing key) yields None."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    cur = bench.kernel_source_hash()
+    (prof / bench.PROFILES["cfg2"]).write_text(
+        f"kernel_source_sha256_16: {cur}\n"
+        "   dram_bytes_per_full_launch: 1.5e6\n"
+        "   warp_instructions_per_path_step: 3.5   (comment)\n")
+    (prof / bench.PROFILES["cfg4"]).write_text(
+        "kernel_source_sha256_16: 0000000000000000\n"
+        "   dram_bytes_per_full_launch: 2.0e8\n")
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: cur)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("cfg2") == 1.5e6
+    assert bench.profiled_value("cfg2", "warp_instructions_per_path_step") == 3.5
+    assert bench.profiled_value("cfg2", "no_such_key") is None
+    assert bench.profiled_traffic("cfg4") is None          # stale source hash
+    assert bench.profiled_traffic("e1") is None            # no summary for this workload
+
+
+def test_issue_roofline_arithmetic(monkeypatch):
+    """achieved = path-steps/s x warp instructions per path-step; peak = 152
+    SMs x 4 schedulers x one warp instruction per cycle at the max SM clock."""
+    monkeypatch.setattr(bench, "profiled_value", lambda config, key: 4.0)
+    r = bench.issue_roofline("cfg2", 1.0e11, 2000.0)
+    assert r["achieved_warp_inst_per_s"] == pytest.approx(4.0e11)
+    assert r["peak_warp_inst_per_s"] == pytest.approx(152 * 4 * 2000e6)
+    assert r["frac"] == pytest.approx(4.0e11 / (152 * 4 * 2000e6))
+    monkeypatch.setattr(bench, "profiled_value", lambda config, key: None)
+    assert bench.issue_roofline("cfg2", 1.0e11, 2000.0) is None
+
+
+def test_committed_profiles_parse():
+    """The committed summaries carry a source hash and the figures bench.py
+    reads (whether or not they match the sources of this checkout)."""
+    import re
+    for name in bench.PROFILES.values():
+        txt = open(os.path.join(bench.ROOT, "profiles", name)).read()
+        assert re.search(r"kernel_source_sha256_16:\s*[0-9a-f]{16}", txt), name
+        assert re.search(r"dram_bytes_per_full_launch:\s*[0-9.eE+]+", txt), name
