@@ -224,8 +224,11 @@ def cpu_baseline(w, budget_s: float = 15.0):
     if secs < 0.5 * budget_s and want < 4000:   # the calibration overestimated a row's cost
         want = int(min(4000, want * budget_s / max(secs, 1e-3)))
         steps, secs, rows = oracle_sample(w, want, threads)
+    distinct = len(set(rows.tolist()))
+    what = (f"{len(rows)} evenly spaced rows" if distinct == len(rows) else
+            f"{len(rows)} rows ({distinct} distinct, each recomputed)")
     return {"value": steps / secs, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(rows)} evenly spaced rows of {w.name} at N={w.n_paths}, "
+            "sample": f"{what} of {w.name} at N={w.n_paths}, "
                       f"dt={w.dt:g} ({steps:.3e} path-steps in {secs:.1f} s, FP64, "
                       f"{threads} threads)"}
 
