@@ -89,6 +89,37 @@ def test_row_sums_equal_b_tabulated(orc):
     assert np.abs(P.dense(val) @ np.ones(P.n) - b).max() < 1e-12
 
 
+@pytest.mark.parametrize("scheme", ["EM", "GM"])
+def test_constant_tables_equal_the_constant_set(orc, scheme):
+    """Bilinear interpolation of a constant table returns the constant (to
+    FP64 rounding of the four weights' sum), so the tabulated set with
+    sigma == s and c == c0 (FP32 tables, f and g as parameters) is the
+    constant set (s, d = 0, c0, f, g) path for path: the same steps and
+    sides, weights and b to 1e-12, under the naive and the Gobet-Menozzi
+    exit.  Pins the table set's f, g and c plumbing and its evaluation at
+    the projections."""
+    s32, c32 = np.float32(1.3), np.float32(-0.7)
+    f, g = 0.45, 1.7
+    tab_s = np.full((9, 13), s32, dtype=np.float32)
+    tab_c = np.full((9, 13), c32, dtype=np.float32)
+    sch = orc.SCHEME_EM if scheme == "EM" else orc.SCHEME_GM
+    T = orc.Problem(grid(3, 4, ext=2), orc.COEF_TABLE, params=(f, g), sigma_tab=tab_s, c_tab=tab_c)
+    C = orc.Problem(grid(3, 4, ext=2), orc.COEF_CONSTANT,
+                    params=(float(s32), 0.0, 0.0, float(c32), f, g))
+    vt, bt, st, rt = T.assemble(60, 2e-3, 21, 100000, records=True, scheme=sch)
+    vc, bc, sc, rc = C.assemble(60, 2e-3, 21, 100000, records=True, scheme=sch)
+    assert np.array_equal(rt["steps"], rc["steps"])
+    assert np.array_equal(rt["side"], rc["side"]) and np.array_equal(rt["flags"], rc["flags"])
+    assert np.array_equal(st, sc)
+    np.testing.assert_allclose(vt, vc, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(bt, bc, rtol=1e-12, atol=1e-14)
+    for key in rt.dtype.names:
+        if rt[key].dtype.kind == "f":
+            np.testing.assert_allclose(rt[key], rc[key], rtol=1e-12, atol=1e-14, err_msg=key)
+        else:
+            assert np.array_equal(rt[key], rc[key]), key
+
+
 def test_tabulated_set_requires_tables(orc):
     """The tabulated coefficient set reads both tables at every step: the
     wrapper refuses to build it without them (or with mismatched shapes)
