@@ -323,3 +323,66 @@ def test_gm_exit_brute_force_variable_sigma(orc):
                 assert (R["steps"], R["side"]) == (K, side), (h, k, p, R, K, side)
                 n_side[side] += 1
     assert np.all(n_side > 0)
+
+
+def _brute_table_path(P, k, p, h, seed, kmax, m, sig, cf):
+    """One naive EM path (Sec. 2.3) with s and c from scipy's linear
+    regular-grid interpolators (a library routine for the bilinear lookup):
+    steps from the knot until the first point outside the closed patch, side
+    of smallest positive overshoot (ties E, N, W, S).  Returns (K, side, Y)."""
+    import oracle
+    x0, y0 = P.xy[k]
+    dxl = (P.grid.x1 - P.grid.x0) / (P.grid.Hx * m)
+    dyl = (P.grid.y1 - P.grid.y0) / (P.grid.Hy * m)
+    i, j = round((x0 - P.grid.x0) / dxl), round((y0 - P.grid.y0) / dyl)
+    ilo, ihi = (i - m, i + m) if i % m == 0 else ((i // m) * m, (i // m) * m + m)
+    jlo, jhi = (j - m, j + m) if j % m == 0 else ((j // m) * m, (j // m) * m + m)
+    xlo, xhi = P.grid.x0 + ilo * dxl, P.grid.x0 + ihi * dxl
+    ylo, yhi = P.grid.y0 + jlo * dyl, P.grid.y0 + jhi * dyl
+    key = np.array([seed & 0xffffffff, seed >> 32], dtype=np.uint32)
+    X, Y, S = x0, y0, 0.0
+    z = None
+    for n in range(kmax):
+        if n % 2 == 0:
+            r = oracle.philox(np.array([[n // 2, p, k, 0]], dtype=np.uint32), key)[0]
+            z = oracle.box_muller(r[0], r[1]) + oracle.box_muller(r[2], r[3])
+        s = float(sig([[Y, X]])[0])
+        S += float(cf([[Y, X]])[0]) * h
+        X, Y = X + s * (math.sqrt(h) * z[2 * (n % 2)]), Y + s * (math.sqrt(h) * z[2 * (n % 2) + 1])
+        ov = [X - xhi, Y - yhi, xlo - X, ylo - Y]
+        pos = [o for o in range(4) if ov[o] > 0]
+        if pos:
+            return n + 1, min(pos, key=lambda o: (ov[o], o)), math.exp(S)
+    return kmax, None, math.exp(S)
+
+
+def test_tabulated_paths_brute_force(orc):
+    """Varying FP32 s and c tables (smooth, 17 x 13 nodes over [0,1]^2, so
+    the lookup is bilinear within cells and the x/y orientation matters): the
+    oracle's (K, side) of every path equals the direct restatement with
+    scipy's interpolators, and its exit weight Y = exp(sum c h) agrees to
+    1e-12."""
+    from scipy.interpolate import RegularGridInterpolator
+    m = 4
+    nx, ny = 17, 13
+    xs, ys = np.linspace(0, 1, nx), np.linspace(0, 1, ny)
+    Xg, Yg = np.meshgrid(xs, ys)  # [ny][nx]
+    sig = (1.2 + 0.4 * np.sin(2.3 * Xg + 0.7) * np.cos(1.9 * Yg) + 0.2 * Xg).astype(np.float32)
+    cfl = (-0.8 + 0.5 * np.cos(3.1 * Yg) * Xg).astype(np.float32)
+    P = orc.Problem(grid(4, m, ext=2), orc.COEF_TABLE, params=(0.0, 1.0), sigma_tab=sig,
+                    c_tab=cfl)
+    si = RegularGridInterpolator((ys, xs), sig.astype(np.float64), method="linear")
+    ci = RegularGridInterpolator((ys, xs), cfl.astype(np.float64), method="linear")
+    seed, h, N = 0x2468_ace0_1357, 1e-3, 40
+    kmax = int(8.0 / h)
+    rows = [knot_at(P, 0.5, 0.5), knot_at(P, 0.25, 0.375), knot_at(P, 0.375, 0.75)]
+    _, _, _, rec = P.assemble(N, h, seed, kmax, rows=rows, records=True)
+    n_side = np.zeros(4, dtype=int)
+    for r, k in enumerate(rows):
+        for p in range(N):
+            K, side, Yx = _brute_table_path(P, k, p, h, seed, kmax, m, si, ci)
+            R = rec[r * N + p]
+            assert (R["steps"], R["side"]) == (K, side), (k, p, R, K, side)
+            assert R["Y"] == pytest.approx(Yx, rel=1e-12)
+            n_side[side] += 1
+    assert np.all(n_side > 0)
