@@ -58,7 +58,8 @@ def kernel_source_hash() -> str:
 
 
 # Committed ncu summary of each single-launch workload's path kernel.
-PROFILES = {"cfg2": "path_kernel_cfg2_ncu.txt", "cfg4": "path_kernel_cfg4_tabulated_ncu.txt"}
+PROFILES = {"cfg2": "path_kernel_cfg2_ncu.txt", "cfg3": "path_kernel_cfg3_batch_ncu.txt",
+            "cfg4": "path_kernel_cfg4_tabulated_ncu.txt"}
 
 
 def profiled_value(config: str, key: str):
@@ -520,8 +521,11 @@ def run_batch(args):
                        "batched_kernel_ms": float(np.mean(kms)), "launch": "one persistent "
                        "kernel for all 16 problems, replayed from a CUDA graph"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "path_kernel",
-                         "flops_per_path_step": FLOPS_PER_STEP[ws[0].coef_id]},
+                         "frac": achieved / peak, "traffic": profiled_traffic("cfg3"),
+                         "kernel": "path_kernel",
+                         "flops_per_path_step": FLOPS_PER_STEP[ws[0].coef_id],
+                         "issue": issue_roofline("cfg3", steps / args.steps / (np.mean(kms) * 1e-3),
+                                                 sm_max)},
             "cpu_baseline": None if args.no_baseline else cpu_baseline_batch(ws),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
