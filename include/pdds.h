@@ -119,7 +119,8 @@ typedef struct {
   int64_t clamped;          /* interface exits clamped to the stencil ends              */
   int64_t units;            /* work units processed                                     */
   int32_t device_error;     /* PDDS_OK, PDDS_ETIMEOUT, or PDDS_EINVAL (an RBF exit found no
-                               table for its stencil: nothing deposited) from the last kernel */
+                               table for its stencil: nothing deposited; or a per-knot budget
+                               outside [0, 2^31): counted as 0) from the last assembly      */
   int32_t solve_iters;      /* iterations of the last pdds_solve                        */
   double solve_relres;      /* ||b - G u|| / ||b|| of the last pdds_solve               */
   float path_kernel_ms;     /* CUDA-event time of the last path kernel (timing on)     */
@@ -188,8 +189,9 @@ pdds_status pdds_set_timing(pdds_ctx* ctx, int32_t on);
  * knots of the side crossed (Eq. 21-22 with a linear scheme; boundary points of
  * the stencil add their known g).  Then G_kk = 1, G_kj = -sum/N_k, b_k = sum/N_k.
  *   n_per_knot: DEVICE int64[n] budgets, or NULL to use n_paths for every knot
- *   n_paths   : >= 1 when n_per_knot is NULL; every N_k must be < 2^31 (a knot
- *               with N_k = 0 keeps row e_k and b_k = 0)
+ *   n_paths   : >= 1 when n_per_knot is NULL; every N_k must be in [0, 2^31) (a
+ *               knot with N_k = 0 keeps row e_k and b_k = 0; the device counts
+ *               any other value as 0 and records PDDS_EINVAL for pdds_stats)
  *   dt        : time step h > 0
  *   seed      : 64-bit Philox4x32-10 key; the normal pair for step 2q and 2q+1 of
  *               path p from knot k comes from counter (q, p, k, tag)
@@ -273,9 +275,11 @@ pdds_status pdds_calibrate(pdds_ctx* ctx, const double* u0, const int64_t* n_per
  *   gap_k = mean d,  V_k = sample variance of phi_GM,  rho_k^2 = corr(phi_GM, xi)^2
  *   h_out[k] = min(h0, 2 h0' eps / (3 |gap_k|))        (h0 when gap_k = 0)
  *   N_out[k] = N_job * max(1, round(9 V_k (1 - rho_k^2) / (eps^2 N_job)))
- * (rounding half to even).  h_out: DEVICE double[n]; N_out: DEVICE int64[n];
- * diag (nullable): DEVICE double[n][3] = gap_k, V_k, rho_k^2.  No context;
- * asynchronous.  EINVAL for n < 1, eps, h0 or h0' not > 0, or N_job < 1. */
+ * (rounding half to even), capped at the largest multiple of N_job below 2^31
+ * so that it is a valid budget (a NaN V_k gives N_job).  h_out: DEVICE
+ * double[n]; N_out: DEVICE int64[n]; diag (nullable): DEVICE double[n][3] =
+ * gap_k, V_k, rho_k^2.  No context; asynchronous.  EINVAL for n < 1, eps, h0
+ * or h0' not > 0, or N_job outside [1, 2^31). */
 pdds_status pdds_plan(const double* moments, int64_t n, double eps, double h0, double h0p,
                       int64_t n_job, double* h_out, int64_t* n_out, double* diag,
                       void* cuda_stream);
@@ -383,14 +387,17 @@ pdds_status pdds_solve_noalloc(const pdds_csr* G, const double* b, double* u, do
 
 /* End-to-end call with HOST buffers: uploads the per-knot budgets, assembles,
  * solves and downloads G (row_ptr, col, val), b and u.  Device scratch is owned
- * by the context.  n_per_knot_host may be NULL.  Synchronizes the stream. */
+ * by the context.  n_per_knot_host may be NULL; EINVAL (nothing launched) if a
+ * budget is outside [0, 2^31).  Synchronizes the stream. */
 pdds_status pdds_assemble_solve_host(pdds_ctx* ctx, const int64_t* n_per_knot_host,
                                      int64_t n_paths, double dt, uint64_t seed, double rtol,
                                      int32_t maxit, int32_t* row_ptr_host, int32_t* col_host,
                                      double* val_host, double* b_host, double* u_host,
                                      void* cuda_stream);
 
-/* Counters of the last assemble / solve (synchronizes the device). */
+/* Counters of the last assemble / solve (synchronizes the device).  Returns
+ * the device error the last assembly recorded (out->device_error: PDDS_ETIMEOUT
+ * or PDDS_EINVAL), else PDDS_OK; the counters are filled in either case. */
 pdds_status pdds_stats(pdds_ctx* ctx, pdds_stats_t* out);
 
 /* Text of the last error on ctx (or of the last failed pdds_create when ctx is

@@ -117,7 +117,10 @@ __global__ void plan_kernel(const double* __restrict__ mom, int64_t n, double ep
   // Eq. 41: (2/3) eps = 2 sqrt(V (1 - rho^2) / N), rounded to k N_job, k >= 1
   const double nraw = 9.0 * var * (1.0 - rho2) / (eps * eps);
   double kj = rint(nraw / (double)n_job);
-  if (kj < 1.0) kj = 1.0;
+  if (!(kj >= 1.0)) kj = 1.0;  // also a NaN variance: one job
+  // N_i stays a valid budget: at most the largest multiple of N_job below 2^31
+  const double kcap = floor(2147483647.0 / (double)n_job);
+  if (kj > kcap) kj = kcap;
   h_out[i] = h;
   n_out[i] = (int64_t)kj * n_job;
   if (diag) {

@@ -477,7 +477,7 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   D.n_paths = Nu;
   if (N) {
     CK(c, pdds::launch_unit_prefix(N, c->geo.n, c->unit_paths, c->d_unit_prefix,
-                                   c->d_path_prefix, s));
+                                   c->d_path_prefix, &c->d_scratch->error, s));
     ++launches;
     D.knot_unit_prefix = c->d_unit_prefix;
     D.path_prefix = c->d_path_prefix;
@@ -1062,9 +1062,9 @@ pdds_status pdds_plan(const double* moments, int64_t n, double eps, double h0, d
   (void)cudaGetLastError();
   if (!moments || !h_out || !n_out)
     return fail(nullptr, PDDS_EINVAL, "plan: moments, h_out and n_out are required");
-  if (n < 1 || !(eps > 0) || !(h0 > 0) || !(h0p > 0) || n_job < 1 || !std::isfinite(eps) ||
-      !std::isfinite(h0) || !std::isfinite(h0p))
-    return fail(nullptr, PDDS_EINVAL, "plan: need n >= 1, eps, h0, h0' > 0 and N_job >= 1");
+  if (n < 1 || !(eps > 0) || !(h0 > 0) || !(h0p > 0) || n_job < 1 || n_job > 0x7fffffffll ||
+      !std::isfinite(eps) || !std::isfinite(h0) || !std::isfinite(h0p))
+    return fail(nullptr, PDDS_EINVAL, "plan: need n >= 1, eps, h0, h0' > 0 and 1 <= N_job < 2^31");
   cudaError_t e = pdds::launch_plan(moments, n, eps, h0, h0p, n_job, h_out, n_out, diag,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, PDDS_ECUDA, std::string("plan: ") + cudaGetErrorString(e));
@@ -1097,7 +1097,7 @@ pdds_status pdds_stats(pdds_ctx* c, pdds_stats_t* out) {
   c->st.units = (int64_t)s.units;
   c->st.device_error = s.error;
   *out = c->st;
-  return s.error ? PDDS_ETIMEOUT : PDDS_OK;
+  return s.error ? (pdds_status)s.error : PDDS_OK;
 }
 
 const char* pdds_last_error(const pdds_ctx* c) {
@@ -1146,6 +1146,9 @@ pdds_status pdds_assemble_solve_host(pdds_ctx* c, const int64_t* N_host, int64_t
   if (!val_host || !b_host || !u_host)
     return fail(c, PDDS_EINVAL, "assemble_solve_host: val, b and u host buffers are required");
   const int64_t n = c->geo.n, nnz = c->geo.nnz;
+  for (int64_t k = 0; N_host && k < n; ++k)
+    if (N_host[k] < 0 || N_host[k] > 0x7fffffffll)
+      return fail(c, PDDS_EINVAL, "assemble_solve_host: every N_k must be in [0, 2^31)");
   cudaStream_t s = (cudaStream_t)stream;
   if (!c->e_rp) {
     CK(c, dalloc(&c->e_N, n));
@@ -1279,11 +1282,16 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
            "pattern copy");
       step(cudaMemsetAsync(G[i]->val, 0, c->geo.nnz * 8, s), "memset");
       step(cudaMemsetAsync(b[i], 0, c->geo.n * 8, s), "memset");
-      if (N && N[i])
-        step(pdds::launch_unit_prefix(N[i], c->geo.n, c0->unit_paths, c->d_unit_prefix,
-                                      c->d_path_prefix, s), "unit prefix");
     }
+    // cleared before the prefixes, which record invalid budgets in it
     step(cudaMemsetAsync(c0->d_scratch, 0, sizeof(pdds::Scratch), s), "memset");
+    for (int i = 0; N && i < count; ++i) {
+      pdds_ctx* c = ctxs[i];
+      if (N[i])
+        step(pdds::launch_unit_prefix(N[i], c->geo.n, c0->unit_paths, c->d_unit_prefix,
+                                      c->d_path_prefix, &c0->d_scratch->error, s),
+             "unit prefix");
+    }
     step(pdds::launch_prob_prefix(c0->d_batch, count, c0->d_prob_prefix, s), "prob prefix");
     if (cap == PDDS_OK) {
       const bool timing = c0->timing;

@@ -78,7 +78,7 @@ struct Scratch {
   unsigned long long truncated;
   unsigned long long clamped;
   unsigned long long units;
-  int32_t error;                  // 0, PDDS_ETIMEOUT or PDDS_EINVAL (missing RBF table)
+  int32_t error;                  // 0, PDDS_ETIMEOUT or PDDS_EINVAL (missing RBF table, bad budget)
   int32_t pad_;
 };
 
@@ -131,8 +131,9 @@ bool path_kernel_has_cv(int coef_id);
 // Control-variate network (pdds_mlp.cu): FP32 theta -> staged image.
 size_t mlp_image_bytes();
 cudaError_t mlp_stage(const float* theta, void* image, cudaStream_t stream);
+// Budgets outside [0, 2^31) count as zero paths and set *err = PDDS_EINVAL.
 cudaError_t launch_unit_prefix(const int64_t* n_per_knot, int64_t n, int64_t unit_paths,
-                               int64_t* knot_unit_prefix, int64_t* path_prefix,
+                               int64_t* knot_unit_prefix, int64_t* path_prefix, int32_t* err,
                                cudaStream_t stream);
 cudaError_t launch_cv_cells(const float* nodes, int nx, int ny, float* cells, cudaStream_t s);
 cudaError_t launch_prob_prefix_single(const ProbDesc& D, int64_t* out, cudaStream_t stream);

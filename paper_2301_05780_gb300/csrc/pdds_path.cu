@@ -14,15 +14,29 @@ namespace pdds {
 namespace {
 
 // ------------------------------------------------------ prefix / finalize
+// A budget outside [0, 2^31) counts as no paths (the knot keeps row e_k).
+__device__ __forceinline__ int64_t checked_budget(int64_t v, bool& bad) {
+  if (v < 0 || v > 0x7fffffffll) { bad = true; return 0; }
+  return v;
+}
+
 // Single block: units and records before each knot (exclusive prefix sums).
+// An invalid budget is skipped and recorded as PDDS_EINVAL in *err.
 __global__ void unit_prefix_kernel(const int64_t* __restrict__ N, int64_t n, int64_t C,
-                                   int64_t* __restrict__ up, int64_t* __restrict__ pp) {
+                                   int64_t* __restrict__ up, int64_t* __restrict__ pp,
+                                   int32_t* __restrict__ err) {
   __shared__ int64_t su[1024], sp[1024];
   const int t = threadIdx.x, T = blockDim.x;
   const int64_t per = (n + T - 1) / T;
   const int64_t lo = min(n, t * per), hi = min(n, lo + per);
   int64_t a = 0, b = 0;
-  for (int64_t i = lo; i < hi; ++i) { a += (N[i] + C - 1) / C; b += N[i]; }
+  bool bad = false;
+  for (int64_t i = lo; i < hi; ++i) {
+    const int64_t v = checked_budget(N[i], bad);
+    a += (v + C - 1) / C;
+    b += v;
+  }
+  if (bad) atomicExch(err, (int32_t)PDDS_EINVAL);
   su[t] = a; sp[t] = b;
   __syncthreads();
   for (int o = 1; o < T; o <<= 1) {
@@ -34,7 +48,8 @@ __global__ void unit_prefix_kernel(const int64_t* __restrict__ N, int64_t n, int
   a = su[t] - a; b = sp[t] - b;  // exclusive
   for (int64_t i = lo; i < hi; ++i) {
     up[i] = a; pp[i] = b;
-    a += (N[i] + C - 1) / C; b += N[i];
+    const int64_t v = checked_budget(N[i], bad);
+    a += (v + C - 1) / C; b += v;
   }
   if (t == T - 1) { up[n] = su[t]; pp[n] = sp[t]; }
 }
@@ -114,8 +129,8 @@ cudaError_t set_path_kernel_smem(int coef, bool rec, int cv, bool ext, size_t sm
 }
 
 cudaError_t launch_unit_prefix(const int64_t* N, int64_t n, int64_t C, int64_t* up, int64_t* pp,
-                               cudaStream_t stream) {
-  unit_prefix_kernel<<<1, 1024, 0, stream>>>(N, n, C, up, pp);
+                               int32_t* err, cudaStream_t stream) {
+  unit_prefix_kernel<<<1, 1024, 0, stream>>>(N, n, C, up, pp, err);
   return cudaGetLastError();
 }
 

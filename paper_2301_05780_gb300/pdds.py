@@ -393,7 +393,7 @@ def pdds_assemble_solve_host(ctx, n_paths, dt, seed, rtol, maxit, row_ptr, col, 
 def pdds_stats(ctx):
     s = pdds_stats_t()
     st = lib().pdds_stats(ctx, C.byref(s))
-    if st not in (PDDS_OK, PDDS_ETIMEOUT):
+    if st != PDDS_OK and st != s.device_error:    # a device error is returned in the dict
         _check(st, ctx)
     return {f: getattr(s, f) for f, _ in s._fields_}
 

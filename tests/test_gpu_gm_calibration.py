@@ -328,6 +328,26 @@ def test_plan_bit_exact(orc):
         pdds.pdds_plan(md, 0.0, 0.08, 0.06, 200, h, Nn)
 
 
+def test_plan_keeps_budgets_valid():
+    """Eq. 41 with a huge variance is capped at the largest multiple of N_job
+    below 2^31, a NaN variance gives one job, an ordinary row is unchanged
+    (9 V / eps^2 = 22500 -> 112 jobs of 200, rounding half to even); N_job at
+    2^31 is refused."""
+    mom = np.zeros((3, 8))
+    mom[:, 0] = 10.0
+    mom[0, 4] = 1e30
+    mom[1, 4] = np.nan
+    mom[2, 4] = 9.0 * 0.25
+    md = torch.tensor(mom, dtype=torch.float64, device="cuda")
+    h = torch.empty(3, dtype=torch.float64, device="cuda")
+    Nn = torch.empty(3, dtype=torch.int64, device="cuda")
+    pdds.pdds_plan(md, 0.01, 0.08, 0.06, 200, h, Nn)
+    torch.cuda.synchronize()
+    assert Nn.cpu().tolist() == [(2**31 - 1) // 200 * 200, 200, 22400]
+    with pytest.raises(pdds.PddsError):
+        pdds.pdds_plan(md, 0.01, 0.08, 0.06, 2**31, h, Nn)
+
+
 # ---------------------------------------------------- the paper's problem
 @pytest.mark.parametrize("scheme", [EM, GM])
 def test_paper_e1_sampled_rows(orc, scheme):

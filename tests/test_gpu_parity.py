@@ -394,6 +394,56 @@ def test_invalid_arguments_are_rejected():
         pdds.pdds_set_launch(P.ctx, block=100)
 
 
+def test_invalid_budgets_count_as_zero_and_are_reported():
+    """Device budgets outside [0, 2^31), which the call cannot read, give their
+    knots no paths (row e_k, b_k = 0), leave every other row as a zero budget
+    there would, and set device_error = EINVAL; the next clean call clears it.
+    The host-buffer call rejects them before any launch."""
+    w = W.config2().scaled(n_paths=1)
+    w.grid = dict(w.grid, Hx=3, Hy=3, m=4)
+    n = pdds.pdds_geometry_host(w.grid)[0].shape[0]
+    Nk = np.array([[200, -1, 300, -5000, 2**31, 100][i % 6] for i in range(n)], np.int64)
+    bad = (Nk < 0) | (Nk >= 2**31)
+    P = pdds.Problem(w)
+    P.n_per_knot = torch.from_numpy(Nk).cuda()
+    P.assemble()
+    st = pdds.pdds_stats(P.ctx)
+    assert st["device_error"] == pdds.PDDS_EINVAL
+    assert st["paths"] == Nk[~bad].sum()
+    ref = run_gpu(w, records=False, n_per_knot=np.where(bad, 0, Nk))
+    assert np.allclose(P.val.cpu().numpy(), ref["val"], rtol=1e-11, atol=1e-14)
+    assert np.allclose(P.b.cpu().numpy(), ref["b"], rtol=1e-11, atol=1e-14)
+    assert np.all(P.b.cpu().numpy()[bad] == 0)
+    P.n_per_knot = torch.from_numpy(np.where(bad, 7, Nk)).cuda()
+    P.assemble()
+    assert pdds.pdds_stats(P.ctx)["device_error"] == 0
+    nnz = P.nnz
+    with pytest.raises(pdds.PddsError) as e:
+        pdds.pdds_assemble_solve_host(P.ctx, 0, w.dt, w.seed, 1e-12, 100, None, None,
+                                      np.zeros(nnz), np.zeros(n), np.zeros(n), n_per_knot=Nk)
+    assert e.value.status == pdds.PDDS_EINVAL
+
+
+def test_invalid_budget_in_a_batch_is_reported():
+    """One problem of a batched launch with a negative budget: the launch's
+    device_error is EINVAL (the error word is cleared before the per-problem
+    prefixes, not after them) and that knot keeps row e_k."""
+    ws = W.config3()[3:5]
+    probs = [pdds.Problem(w) for w in ws]
+    for P, w in zip(probs, ws):
+        P.n_per_knot = torch.from_numpy(np.minimum(w.budgets(P.n), 300)).cuda()
+    probs[1].n_per_knot[2] = -7
+    pdds.pdds_assemble_batch([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs],
+                             0, [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
+    st = pdds.pdds_stats(probs[0].ctx)
+    assert st["device_error"] == pdds.PDDS_EINVAL
+    P = probs[1]
+    rp, col, val = P.row_ptr.cpu().numpy(), P.col.cpu().numpy(), P.val.cpu().numpy()
+    s_, e_ = rp[2], rp[3]
+    assert np.all(val[s_:e_][col[s_:e_] == 2] == 1.0) and np.all(val[s_:e_][col[s_:e_] != 2] == 0)
+    assert P.b[2].item() == 0.0
+
+
 def test_bounded_wait_reports_timeout_without_hanging():
     """With a 1 ns wait limit every warp that would wait for a work unit gives up
     at once: the kernel returns and pdds_stats reports PDDS_ETIMEOUT; the
