@@ -23,6 +23,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -109,12 +110,18 @@ def issue_roofline(config: str, path_steps_per_s: float, sm_max_mhz: float):
                       "clock"}
 
 
+# Directory for the raw nvidia-smi samples (--clocks-dir); a temporary one
+# when unset.  The JSON line carries their summary either way.
+CLOCKS_DIR = None
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        d = CLOCKS_DIR or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
@@ -462,7 +469,13 @@ def main():
                     help="stencil interpolation of the e1 pipeline (Sec. 2.1 RBF or linear)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiling runs count launches)")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="keep the raw nvidia-smi samples of the timed region in this directory")
     args = ap.parse_args()
+    global CLOCKS_DIR
+    if args.clocks_dir:
+        os.makedirs(args.clocks_dir, exist_ok=True)
+        CLOCKS_DIR = args.clocks_dir
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
