@@ -50,3 +50,27 @@ def test_committed_profiles_parse():
         txt = open(os.path.join(bench.ROOT, "profiles", name)).read()
         assert re.search(r"kernel_source_sha256_16:\s*[0-9a-f]{16}", txt), name
         assert re.search(r"dram_bytes_per_full_launch:\s*[0-9.eE+]+", txt), name
+
+
+def test_source_hash_covers_the_path_kernel_include_closure():
+    """The hash gating the committed figures spans exactly the files compiled
+    into the path kernel: every csrc/ file that instantiates the template, and
+    every csrc/ header reachable from path_kernel.cuh by #include."""
+    import re
+    csrc = os.path.join(bench.ROOT, "paper_2301_05780_gb300", "csrc")
+
+    def local_includes(name):
+        txt = open(os.path.join(csrc, name)).read()
+        return [f for f in re.findall(r'#include\s+"([^"]+)"', txt)
+                if os.path.exists(os.path.join(csrc, f))]
+
+    closure, todo = set(), ["path_kernel.cuh"]
+    while todo:
+        f = todo.pop()
+        if f not in closure:
+            closure.add(f)
+            todo.extend(local_includes(f))
+    users = {f for f in os.listdir(csrc) if f.endswith(".cu")
+             and "&path_kernel<" in open(os.path.join(csrc, f)).read()}
+    assert len(users) == 6
+    assert set(bench.PATH_KERNEL_SOURCES) == closure | users
