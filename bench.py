@@ -331,16 +331,21 @@ def run_gpu(args):
         launch = pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed)  # before warm-up, untimed
     pdds.pdds_set_timing(P.ctx, True)
 
-    def step(asm_ev=None):
+    def step(step_ev=None, asm_ev=None):
+        # the step's events bracket assembly + solve only; one pdds_stats after
+        # them reads the counters and the path-kernel time of the assembly, so
+        # no host synchronization falls between the two calls
+        if step_ev:
+            step_ev[0].record(stream)
         if asm_ev:
             asm_ev[0].record(stream)
         P.assemble(stream)
         if asm_ev:
             asm_ev[1].record(stream)
-        st = pdds.pdds_stats(P.ctx)
         P.solve(rtol=1e-12, maxit=5000, stream=stream)
-        st2 = pdds.pdds_stats(P.ctx)
-        return st, st2
+        if step_ev:
+            step_ev[1].record(stream)
+        return pdds.pdds_stats(P.ctx)
 
     for _ in range(args.warmup):
         step()
@@ -357,14 +362,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()                    # evict L2 between timed steps
-            ev[i][0].record(stream)
-            st, st2 = step(asm_ev[i])
-            ev[i][1].record(stream)
+            st = step(ev[i], asm_ev[i])
             path_ms.append(st["path_kernel_ms"])
             steps_done += st["path_steps"]
-            launches += st2["kernel_launches"]
+            launches += st["kernel_launches"]
             errors += st["device_error"]
-            iters.append(st2["solve_iters"])
+            iters.append(st["solve_iters"])
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     asm_ms = [a.elapsed_time(b) for a, b in asm_ev]
@@ -505,24 +508,28 @@ def run_batch(args):
     args_b = ([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs], 0,
               [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
 
-    def step():
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        # events around the batched assembly and the 16 solves; the counters
+        # and the batched graph's time are read once, after them
+        if ev:
+            ev[0].record(stream)
         pdds.pdds_assemble_batch(*args_b)
-        st = pdds.pdds_stats(c0)
         for P in probs:
             P.solve(rtol=1e-12, maxit=5000)
-        return st
+        if ev:
+            ev[1].record(stream)
+        return pdds.pdds_stats(c0)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
     kms, steps, t_ms = [], 0, 0.0
     with Clocks(0) as clk:
         for _ in range(args.steps):
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            st = step()
-            b_.record(stream)
+            st = step((a, b_))
             torch.cuda.synchronize()
             t_ms += a.elapsed_time(b_)
             kms.append(st["path_kernel_ms"])

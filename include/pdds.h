@@ -178,7 +178,9 @@ pdds_status pdds_autotune(pdds_ctx* ctx, int64_t n_paths, double dt, uint64_t se
 pdds_status pdds_set_wait_limit(pdds_ctx* ctx, double seconds);
 
 /* When on, the path kernel is bracketed by CUDA events on the caller's stream
- * and its duration is reported in pdds_stats (the call then synchronizes). */
+ * (pdds_assemble_batch: the whole batched graph).  The assembly does not wait
+ * for them; pdds_stats, which synchronizes, reports the duration of the last
+ * timed assembly in path_kernel_ms. */
 pdds_status pdds_set_timing(pdds_ctx* ctx, int32_t on);
 
 /* Monte Carlo assembly of G and b (Eq. 24-25), the hot path.

@@ -224,6 +224,7 @@ struct pdds_ctx {
   int64_t unit_paths = 4096;
   int64_t k_max = 0;
   bool timing = false;
+  bool timing_pending = false;  // ev0/ev1 recorded around a path kernel, time not read yet
   double wait_s = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // solver scratch
@@ -280,6 +281,16 @@ pdds_status cuda_fail(pdds_ctx* c, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
+
+// The path-kernel time of the last timed assembly: waits for its end event
+// only here, so that timing adds no host synchronization to the assembly.
+pdds_status read_timing(pdds_ctx* c) {
+  if (!c->timing_pending) return PDDS_OK;
+  c->timing_pending = false;
+  CK(c, cudaEventSynchronize(c->ev1));
+  CK(c, cudaEventElapsedTime(&c->st.path_kernel_ms, c->ev0, c->ev1));
+  return PDDS_OK;
+}
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -464,6 +475,7 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   if (pdds_status e = check_csr(c, G, b)) return e;
   const int64_t kmax = c->k_max > 0 ? c->k_max : default_kmax(c, dt);
   c->st = pdds_stats_t{};
+  c->timing_pending = false;
   int launches = 0;
   CK(c, cudaMemcpyAsync(G->row_ptr, c->d_row_ptr, (c->geo.n + 1) * 4, cudaMemcpyDeviceToDevice, s));
   CK(c, cudaMemcpyAsync(G->col, c->d_col, c->geo.nnz * 4, cudaMemcpyDeviceToDevice, s));
@@ -497,10 +509,7 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   CK(c, pdds::launch_finalize(G->row_ptr, G->col, G->val, b, N, Nu, c->geo.n, s));
   ++launches;
   c->st.kernel_launches = launches;
-  if (c->timing) {
-    CK(c, cudaEventSynchronize(c->ev1));
-    CK(c, cudaEventElapsedTime(&c->st.path_kernel_ms, c->ev0, c->ev1));
-  }
+  c->timing_pending = c->timing;
   return PDDS_OK;
 }
 
@@ -823,6 +832,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
     c->unit_paths = sh.unit;
     c->exit_batch = sh.batch;
     st = assemble_impl(c, N, Nu, dt, seed, &G, b, nullptr, s);
+    if (st == PDDS_OK) st = read_timing(c);
     if (st == PDDS_OK) ms = std::min(ms, c->st.path_kernel_ms);
   };
   // first pass: every shape once on the sample; second pass: the best twelve again
@@ -1090,6 +1100,7 @@ pdds_status pdds_stats(pdds_ctx* c, pdds_stats_t* out) {
   pdds::Scratch s{};
   CK(c, cudaDeviceSynchronize());
   CK(c, cudaMemcpy(&s, c->d_scratch, sizeof(s), cudaMemcpyDeviceToHost));
+  if (pdds_status e = read_timing(c)) return e;
   c->st.path_steps = (int64_t)s.steps;
   c->st.paths = (int64_t)s.paths;
   c->st.truncated = (int64_t)s.truncated;
@@ -1314,12 +1325,12 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
     c0->graph_key = key;
   }
   c0->st = pdds_stats_t{};
+  c0->timing_pending = false;
   if (c0->timing) CK(c0, cudaEventRecord(c0->ev0, s));
   CK(c0, cudaGraphLaunch(c0->graph, s));
   if (c0->timing) {
     CK(c0, cudaEventRecord(c0->ev1, s));
-    CK(c0, cudaEventSynchronize(c0->ev1));
-    CK(c0, cudaEventElapsedTime(&c0->st.path_kernel_ms, c0->ev0, c0->ev1));
+    c0->timing_pending = true;
   }
   int launches = 2 + count;
   for (int i = 0; i < count; ++i) launches += (N && N[i]) ? 1 : 0;

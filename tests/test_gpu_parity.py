@@ -394,6 +394,35 @@ def test_invalid_arguments_are_rejected():
         pdds.pdds_set_launch(P.ctx, block=100)
 
 
+def test_timing_is_read_by_stats():
+    """With timing on the assembly only records its events: pdds_stats reports
+    a path-kernel time no longer than the whole call timed from outside; with
+    timing off it reports 0.  The batched launch reports its graph's time."""
+    w = W.config2().scaled(n_paths=2000)
+    P = pdds.Problem(w)
+    pdds.pdds_set_timing(P.ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    P.assemble()
+    b.record()
+    P.solve()
+    st = pdds.pdds_stats(P.ctx)
+    outer = a.elapsed_time(b)
+    assert 0 < st["path_kernel_ms"] <= outer * 1.01 + 0.01, (st["path_kernel_ms"], outer)
+    assert st["solve_iters"] > 0 and st["device_error"] == 0
+    pdds.pdds_set_timing(P.ctx, False)
+    P.assemble()
+    assert pdds.pdds_stats(P.ctx)["path_kernel_ms"] == 0
+    ws = W.config3()[3:5]
+    probs = [pdds.Problem(x) for x in ws]
+    for Q, x in zip(probs, ws):
+        Q.n_per_knot = torch.from_numpy(np.minimum(x.budgets(Q.n), 200)).cuda()
+    pdds.pdds_set_timing(probs[0].ctx, True)
+    pdds.pdds_assemble_batch([Q.ctx for Q in probs], [Q.G for Q in probs], [Q.b for Q in probs],
+                             0, [Q.n_per_knot for Q in probs], ws[0].dt, ws[0].seed)
+    assert pdds.pdds_stats(probs[0].ctx)["path_kernel_ms"] > 0
+
+
 def test_invalid_budgets_count_as_zero_and_are_reported():
     """Device budgets outside [0, 2^31), which the call cannot read, give their
     knots no paths (row e_k, b_k = 0), leave every other row as a zero budget
