@@ -1,0 +1,132 @@
+"""Error of the solved interfacial u (Eq. 23) for each workload, through the C ABI.
+
+Two figures per workload:
+  * against the closed-form u, where the workload has one, at its full path
+    budgets (Monte Carlo error plus the O(sqrt h) bias of the naive exit);
+  * against the FP64 oracle on the same Philox streams, at budgets the
+    oracle finishes in seconds: both sides draw the same Gaussians, so the
+    difference is the FP32 path arithmetic alone (the rare exit decisions
+    that flip near a side, and the rounding of the weights).
+Each test prints its figures on one line beginning "u-error".  The bounds
+are about ten times the figures measured on a GB300 (the runs are seeded, so
+they move only if the FP32 rounding of the paths changes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2301_05780_gb300 import pdds, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def exact_u(coef_id, xy):
+    """The closed-form solutions the workloads are built on (None: tabulated
+    coefficients, no closed form)."""
+    x, y = xy[:, 0], xy[:, 1]
+    if coef_id == W.COEF_LAPLACE_EXPSIN:
+        return np.exp(x) * np.sin(y)
+    if coef_id == W.COEF_MANUFACTURED:
+        return np.sin(math.pi * x) * np.cos(math.pi * y) + x * y
+    if coef_id == W.COEF_VARSIGMA:
+        return np.exp(x / 4) * np.cos(y / 2)
+    return None
+
+
+def rms(a):
+    return float(np.sqrt(np.mean(np.square(a))))
+
+
+def gpu_u(w, n_per_knot=None):
+    P = pdds.Problem(w)
+    if n_per_knot is not None:
+        P.n_per_knot = torch.from_numpy(np.asarray(n_per_knot, dtype=np.int64)).cuda()
+    P.assemble()
+    P.solve(rtol=1e-12)
+    torch.cuda.synchronize()
+    assert pdds.pdds_stats(P.ctx)["device_error"] == 0
+    return P.u.cpu().numpy(), pdds.pdds_knot_coords(P.ctx)
+
+
+def oracle_u(orc, w, n_paths, tag=0):
+    tabs = w.tables if w.coef_id == W.COEF_TABLE else (None, None)
+    O = orc.Problem(w.grid, w.coef_id, w.params, *tabs)
+    val, b, _, _ = O.assemble(n_paths, w.dt, w.seed, w.k_max, tag=tag)
+    u, rc, _, _ = O.bicgstab(val, b, rtol=1e-13)
+    assert rc == 0
+    return u, O.xy
+
+
+def check_single(orc, w, n_oracle, tol_exact, tol_oracle):
+    line = [f"u-error {w.name}"]
+    if tol_exact is not None:
+        u, xy = gpu_u(w)
+        ex = exact_u(w.coef_id, xy)
+        e = rms(u - ex)
+        line.append(f"vs exact {e:.3e} (max {np.abs(u - ex).max():.3e}) at N={w.n_paths}")
+        assert e < tol_exact
+    wr = w.scaled(n_paths=n_oracle)
+    ug, xyg = gpu_u(wr)
+    uo, xyo = oracle_u(orc, wr, n_oracle)
+    assert np.allclose(xyg, xyo)
+    d = rms(ug - uo)
+    line.insert(1, f"n={ug.size}")
+    line.append(f"vs oracle {d:.3e} (max {np.abs(ug - uo).max():.3e}) at N={n_oracle}")
+    print("; ".join(line))
+    assert d < tol_oracle
+
+
+def test_config1_u_error(orc):
+    check_single(orc, W.config1(), 10_000, 2e-2, 2e-5)
+
+
+def test_config2_u_error(orc):
+    check_single(orc, W.config2(), 2000, 2e-2, 1e-5)
+
+
+def test_config4_u_error(orc):
+    check_single(orc, W.config4(), 30, None, 1e-5)
+
+
+def test_config5_u_error(orc):
+    check_single(orc, W.config5(), 500, 5e-2, 1e-4)
+
+
+def test_config3_u_error(orc):
+    """All 16 problems in one batched launch at their full budgets against
+    the closed form; against the oracle (Philox tag i for problem i) with
+    every budget clamped to 30 paths."""
+    ws = W.config3()
+    probs = [pdds.Problem(w) for w in ws]
+
+    def batch(cap=None):
+        for P, w in zip(probs, ws):
+            Nk = w.budgets(P.n) if cap is None else np.minimum(w.budgets(P.n), cap)
+            P.n_per_knot = torch.from_numpy(Nk).cuda()
+        pdds.pdds_assemble_batch([P.ctx for P in probs], [P.G for P in probs],
+                                 [P.b for P in probs], 0, [P.n_per_knot for P in probs],
+                                 ws[0].dt, ws[0].seed)
+        assert pdds.pdds_stats(probs[0].ctx)["device_error"] == 0
+        out = []
+        for P in probs:
+            P.solve(rtol=1e-12)
+            out.append(P.u.cpu().numpy())
+        return out
+
+    full = batch()
+    err = np.concatenate([u - exact_u(w.coef_id, pdds.pdds_knot_coords(P.ctx))
+                          for u, w, P in zip(full, ws, probs)])
+    cap = 30
+    red = batch(cap)
+    diffs = []
+    for i, (u, w, P) in enumerate(zip(red, ws, probs)):
+        uo, _ = oracle_u(orc, w, np.minimum(w.budgets(P.n), cap).astype(np.int64), tag=i)
+        diffs.append(u - uo)
+    d = np.concatenate(diffs)
+    print(f"u-error cfg3_batch16: n={err.size}; vs exact {rms(err):.3e} (max "
+          f"{np.abs(err).max():.3e}) at budgets log-uniform [1e4, 1e5]; vs oracle {rms(d):.3e} "
+          f"(max {np.abs(d).max():.3e}) at budgets clamped to {cap}")
+    assert rms(err) < 1e-2
+    assert rms(d) < 1e-4
