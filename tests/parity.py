@@ -67,6 +67,7 @@ def compare_rows(gpu, orc, rows, Nk, n, max_flag_frac=1e-3, b_extra_tol=None, at
     side_g = rg["side_flags"] & 0xFF
     flag = (rg["steps"] != ro["steps"]) | (side_g != ro["side"])
     frac = flag.mean()
+    print(f"flagged-paths {frac:.3e} of {flag.size} paths")
     assert frac <= max_flag_frac, f"flagged fraction {frac:.2e}"
     # raw sums: -G_kj N_k and b_k N_k
     Gg = -dense_rows(gpu["row_ptr"], gpu["col"], gpu["val"], rows, n) * Nk[:, None]
