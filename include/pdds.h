@@ -206,7 +206,8 @@ pdds_status pdds_assemble(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_pa
 
 /* Same as pdds_assemble, plus one pdds_path_record per path written to the
  * DEVICE array `records`, laid out knot by knot (knot-major, then path index);
- * it must hold sum_k N_k records. */
+ * it must hold sum_k N_k records (a budget outside [0, 2^31) counts as 0
+ * there too). */
 pdds_status pdds_assemble_records(pdds_ctx* ctx, const int64_t* n_per_knot, int64_t n_paths,
                                   double dt, uint64_t seed, pdds_csr* G, double* b,
                                   pdds_path_record* records, void* cuda_stream);
