@@ -525,11 +525,15 @@ def run_batch(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    kms, steps, t_ms = [], 0, 0.0
+    kms, steps, t_ms, launches = [], 0, 0.0, 0
+    # problem 0's counters restart with every batched launch; the other
+    # contexts only solve, and their launch counters keep adding up
+    others0 = [pdds.pdds_stats(P.ctx)["kernel_launches"] for P in probs[1:]]
     with Clocks(0) as clk:
         for _ in range(args.steps):
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             st = step((a, b_))
+            launches += st["kernel_launches"]
             torch.cuda.synchronize()
             t_ms += a.elapsed_time(b_)
             kms.append(st["path_kernel_ms"])
@@ -556,6 +560,8 @@ def run_batch(args):
                          "issue": issue_roofline("cfg3", steps / args.steps / (np.mean(kms) * 1e-3),
                                                  sm_max)},
             "cpu_baseline": None if args.no_baseline else cpu_baseline_batch(ws),
+            "gpu_launches": launches + sum(pdds.pdds_stats(P.ctx)["kernel_launches"] - k0
+                                           for P, k0 in zip(probs[1:], others0)),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
