@@ -74,3 +74,22 @@ def test_source_hash_covers_the_path_kernel_include_closure():
              and "&path_kernel<" in open(os.path.join(csrc, f)).read()}
     assert len(users) == 6
     assert set(bench.PATH_KERNEL_SOURCES) == closure | users
+
+
+def test_reference_arm_prints_its_line():
+    """`bench.py --impl reference` times the oracle on the host cores and prints
+    one JSON line with the keys the comparison needs (config 1: a sample of
+    under a second)."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                          "reference", "--config", "cfg1", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "path-steps/s"
+    assert line["value"] > 0 and line["steps"] == 2 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "path-steps/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "cfg1_laplace_2x2"
