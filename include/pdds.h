@@ -291,7 +291,10 @@ pdds_status pdds_plan(const double* moments, int64_t n, double eps, double h0, d
  * launch: paths of all problems share one work queue.  Arrays have `count`
  * entries; n_per_knot[i] may be NULL (then n_paths is used).  Problem i uses
  * Philox tag i, so its streams differ from problem 0's.  The sequence is
- * captured once into a CUDA graph per (count, ctxs) and replayed. */
+ * captured once into a CUDA graph per (count, ctxs) and replayed.  Budgets
+ * follow pdds_assemble (outside [0, 2^31): no paths, PDDS_EINVAL recorded).
+ * The launch's counters, device error and time are those of ctxs[0]: read
+ * them with pdds_stats(ctxs[0]). */
 pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
                                 const int64_t* const* n_per_knot, int64_t n_paths, double dt,
                                 uint64_t seed, pdds_csr* const* G, double* const* b,
