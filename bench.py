@@ -1,11 +1,15 @@
 """Benchmark of the PDDSparse hot path on GB300: Monte Carlo assembly of
-G(w) u = b(w) (Eq. 24-25) plus its FP64 solve (Eq. 23), on the config-2
-workload (manufactured u = sin(pi x)cos(pi y) + xy on [0,1]^2, 8x8 subdomains,
-833 knots, N = 1e5 paths per knot, dt = 1e-5).
+G(w) u = b(w) (Eq. 24-25) plus its FP64 solve (Eq. 23).
 
-One step = one full assemble + solve of that system.  Prints one JSON line.
+Default workload: config 3, the largest single-GPU configuration -- 16
+independent BVPs on [0,4]^2 (subdomain grids 4x4 to 32x32, m = 8, variable
+sigma, c = -1, per-knot budgets log-uniform in [1e4, 1e5], dt = 1e-5,
+105,813 knots, ~1.56e12 path-steps) assembled in ONE persistent launch
+replayed from a CUDA graph, then 16 FP64 solves.  One step = that whole batch.
+``--config cfg2`` times the single manufactured problem (8x8 subdomains, 833
+knots, N = 1e5, dt = 1e-5) instead.  Prints one JSON line.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config cfg2]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config cfg3]
 
 N > 1 runs under torchrun, one process per GPU; every rank assembles an
 independent replica (its own seed), so per-GPU work is fixed (weak scaling)
@@ -272,10 +276,53 @@ def cpu_baseline_batch(ws, budget_s: float = 15.0):
                       f"{secs:.1f} s, FP64, {threads} threads)"}
 
 
+def run_reference_batch(args):
+    """The oracle on the batched config-3 workload: every step is a bounded
+    sample of the 16 problems (`threads` evenly spaced rows of each, every row
+    at the same fraction of its own per-knot budget), the fraction chosen by a
+    short calibration pass so that one step takes about 4 s of host time."""
+    ws = workload("cfg3")
+    threads = os.cpu_count() or 1
+
+    def sweep(frac):
+        steps = secs = 0.0
+        for w in ws:
+            s_, t_, _ = oracle_sample(w, threads, threads, frac)
+            steps, secs = steps + s_, secs + t_
+        return steps, secs
+
+    _, secs = sweep(0.002)
+    frac = float(min(1.0, max(0.001, 0.002 * 4.0 / max(secs, 1e-9))))
+    for _ in range(args.warmup):
+        sweep(frac)
+    tot_steps, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        s_, t_ = sweep(frac)
+        tot_steps += s_
+        tot_s += t_
+    v = tot_steps / tot_s
+    sample = (f"{threads} evenly spaced rows of each of the {len(ws)} problems per step, each at "
+              f"{100 * frac:.2f} % of its per-knot budget (FP64 oracle, {threads} threads)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "path-steps/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg3_batch16", "problems": len(ws), "dt": ws[0].dt,
+                       "sample_budget_fraction": frac},
+            "cpu_baseline": {"value": v, "unit": "path-steps/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
+    if args.config == "cfg3":
+        return run_reference_batch(args)
     w = workload(args.config)
     threads = os.cpu_count() or 1
     rows_per_step = max(threads, 2 * threads)
@@ -456,10 +503,12 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 10 for the batched config 3, 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "e1"])
+    ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "e1"],
+                    help="workload (default: config 3, the largest single-GPU configuration)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per knot (small profiling cases; not a bench line)")
     ap.add_argument("--no-baseline", action="store_true",
@@ -479,6 +528,8 @@ def main():
     if args.clocks_dir:
         os.makedirs(args.clocks_dir, exist_ok=True)
         CLOCKS_DIR = args.clocks_dir
+    if args.steps is None:
+        args.steps = 10 if args.config == "cfg3" else 20
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
@@ -493,31 +544,45 @@ def main():
 
 
 def run_batch(args):
-    """Config 3: 16 independent BVPs, per-knot budgets, one persistent launch
-    (captured once into a CUDA graph and replayed) + 16 solves per step."""
+    """Config 3: 16 independent BVPs with per-knot budgets in ONE persistent
+    launch (captured once into a CUDA graph and replayed) plus the 16 FP64
+    solves; one step = that whole batch.  Under torchrun every rank runs an
+    independent replica of the batch (its own seed): weak scaling, no
+    data-path collective."""
     import torch
     from paper_2301_05780_gb300 import pdds
-    torch.cuda.set_device(0)
+
+    rank, local, world = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ws = workload("cfg3")
-    probs = [pdds.Problem(w) for w in ws]
+    seed = replica_seed(ws[0].seed, rank)
+    for w in ws:
+        w.seed = seed
+    probs = [pdds.Problem(w, device=local) for w in ws]
     if args.paths:
         for P in probs:
             P.n_per_knot = torch.clamp(P.n_per_knot, max=args.paths)
     c0 = probs[0].ctx
+    launch = pdds.pdds_get_launch(c0)
     pdds.pdds_set_timing(c0, True)
-    args_b = ([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs], 0,
-              [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
-
     stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    args_b = ([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs], 0,
+              [P.n_per_knot for P in probs], ws[0].dt, seed)
 
     def step(ev=None):
         # events around the batched assembly and the 16 solves; the counters
         # and the batched graph's time are read once, after them
         if ev:
             ev[0].record(stream)
-        pdds.pdds_assemble_batch(*args_b)
+        pdds.pdds_assemble_batch(*args_b, stream=stream)
         for P in probs:
-            P.solve(rtol=1e-12, maxit=5000)
+            P.solve(rtol=1e-12, maxit=5000, stream=stream)
         if ev:
             ev[1].record(stream)
         return pdds.pdds_stats(c0)
@@ -525,44 +590,109 @@ def run_batch(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    kms, steps, t_ms, launches = [], 0, 0.0, 0
+    if world > 1:
+        torch.distributed.barrier()
+    kms, steps, t_ms, launches, errors = [], 0, 0.0, 0, 0
     # problem 0's counters restart with every batched launch; the other
     # contexts only solve, and their launch counters keep adding up
     others0 = [pdds.pdds_stats(P.ctx)["kernel_launches"] for P in probs[1:]]
-    with Clocks(0) as clk:
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
         for _ in range(args.steps):
+            flush.zero_()                    # evict L2 between timed steps
             a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             st = step((a, b_))
             launches += st["kernel_launches"]
+            errors += st["device_error"]
             torch.cuda.synchronize()
             t_ms += a.elapsed_time(b_)
             kms.append(st["path_kernel_ms"])
             steps += st["path_steps"]
-    value = steps / (t_ms * 1e-3)
+    launches += sum(pdds.pdds_stats(P.ctx)["kernel_launches"] - k0
+                    for P, k0 in zip(probs[1:], others0))
+    t_max, steps_all = reduce_timing(t_ms, float(steps), device="cuda")
+    value = steps_all / (t_max * 1e-3)
+
+    # ---- end to end through the host-buffer C-ABI batch call (pinned buffers):
+    # budgets up; G, b and u of all 16 problems down, every step
+    pin = dict(pin_memory=True)
+    Nh = [P.n_per_knot.cpu().pin_memory() for P in probs]
+    rp = [torch.empty(P.n + 1, dtype=torch.int32, **pin) for P in probs]
+    col = [torch.empty(P.nnz, dtype=torch.int32, **pin) for P in probs]
+    val = [torch.empty(P.nnz, dtype=torch.float64, **pin) for P in probs]
+    bh = [torch.empty(P.n, dtype=torch.float64, **pin) for P in probs]
+    uh = [torch.empty(P.n, dtype=torch.float64, **pin) for P in probs]
+    pdds.pdds_set_timing(c0, False)
+    ctxs = [P.ctx for P in probs]
+    e2e_steps = 0 if args.no_baseline else max(2, min(args.steps, 3))
+
+    def e2e_call():
+        return pdds.pdds_assemble_solve_batch_host(ctxs, 0, ws[0].dt, seed, 1e-12, 5000, rp, col,
+                                                   val, bh, uh, n_per_knot=Nh, stream=stream)
+    e2e_val, e2e_check = None, None
+    if e2e_steps:
+        e2e_call()                                    # captures its graph (untimed)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        e2e_path_steps = 0
+        for _ in range(e2e_steps):
+            e2e_call()
+            e2e_path_steps += pdds.pdds_stats(c0)["path_steps"]
+        e2e_s = time.perf_counter() - t0
+        e2e_max, e2e_all = reduce_timing(e2e_s * 1e3, float(e2e_path_steps), device="cuda")
+        e2e_val = e2e_all / (e2e_max * 1e-3)
+        # the host copies hold the same G, b, u as the device call on the same streams
+        u_dev = probs[0].u.cpu().numpy()
+        e2e_check = {"copies_declared": True,
+                     "u0_max_abs_diff_vs_device_call": float(np.abs(uh[0].numpy() - u_dev).max())}
+    h2d = sum(P.n * 8 for P in probs)
+    d2h = sum((P.n + 1) * 4 + P.nnz * 4 + P.nnz * 8 + 2 * P.n * 8 for P in probs)
+
+    # interface error against the closed form (last timed step, all problems)
+    err = np.concatenate([P.u.cpu().numpy() - exact_solution(w.coef_id, pdds.pdds_knot_coords(P.ctx))
+                          for P, w in zip(probs, ws)])
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
     peaks, src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = steps / args.steps * FLOPS_PER_STEP[ws[0].coef_id] / (np.mean(kms) * 1e-3) / 1e12
-    line = {"metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+    fpk = FLOPS_PER_STEP[ws[0].coef_id]
+    kernel_s = float(np.mean(kms)) * 1e-3
+    achieved = steps / args.steps * fpk / kernel_s / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "cfg3_batch16", "problems": len(ws),
                        "H": [w.grid["Hx"] for w in ws], "knots": sum(P.n for P in probs),
                        "paths": sum(P.total_paths() for P in probs), "dt": ws[0].dt,
                        "path_steps_per_step": steps / args.steps,
-                       "batched_kernel_ms": float(np.mean(kms)), "launch": "one persistent "
-                       "kernel for all 16 problems, replayed from a CUDA graph"},
+                       "batched_kernel_ms": float(np.mean(kms)),
+                       "solve": "16 FP64 BiCGSTAB solves to 1e-12 inside each step",
+                       "interface_rms_error": float(np.sqrt(np.mean(err ** 2))),
+                       "accumulation": "f64", "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "launch": {"block": launch[0], "unit_paths": launch[2],
+                                  "exit_batch": launch[3], "kind": "one persistent kernel for "
+                                  "all 16 problems, replayed from a CUDA graph"}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": profiled_traffic("cfg3"),
-                         "kernel": "path_kernel",
-                         "flops_per_path_step": FLOPS_PER_STEP[ws[0].coef_id],
-                         "issue": issue_roofline("cfg3", steps / args.steps / (np.mean(kms) * 1e-3),
-                                                 sm_max)},
+                         "kernel": "path_kernel", "flops_per_path_step": fpk,
+                         "issue": issue_roofline("cfg3", steps / args.steps / kernel_s, sm_max),
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                        f"({src} max SM clock)"},
             "cpu_baseline": None if args.no_baseline else cpu_baseline_batch(ws),
-            "gpu_launches": launches + sum(pdds.pdds_stats(P.ctx)["kernel_launches"] - k0
-                                           for P, k0 in zip(probs[1:], others0)),
-            "clocks": clk.summary()}
+            "e2e": {"value": e2e_val, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "call": "pdds_assemble_solve_batch_host (pinned host buffers)"},
+            "e2e_check": e2e_check,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "device_errors": errors}
     print(json.dumps(line), flush=True)
     return 0
 

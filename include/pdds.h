@@ -70,8 +70,9 @@ enum {
   PDDS_COEF_VARSIGMA = 2,       /* s = sqrt2 (1 + 0.3 sin 2pi x sin 2pi y), d = 0, c = -1,
                                    f = L u for u = e^{x/4} cos(y/2), g = u              */
   PDDS_COEF_TABLE = 3,          /* s and c bilinear in FP32 tables, d = 0,
-                                   f = params[0], g = params[1] (constants)           */
-  PDDS_COEF_CONSTANT = 4,       /* s = p0, d = (p1, p2), c = p3, f = p4, g = p5        */
+                                   f = params[0], g = params[1] (constants); every c
+                                   value <= 0, every s value finite and nonzero      */
+  PDDS_COEF_CONSTANT = 4,       /* s = p0 != 0, d = (p1, p2), c = p3 <= 0, f = p4, g = p5 */
   PDDS_COEF_POISSON_E1 = 5      /* Sec. 5.1, Eq. 42-43: Lap u = f on [-100,100]^2, i.e.
                                    s = sqrt2, d = 0, c = 0, f = Lap u and g = u for
                                    u = 3 + sin(r)/3 + tanh(q)/3, r = sqrt(1 + x^2/100
@@ -137,7 +138,9 @@ pdds_status pdds_geometry_host(const pdds_grid* grid, int64_t* n, int64_t* nnz,
 /* Builds the problem on the current device: knot table, patch boxes, stencil
  * slots, CSR pattern (Sec. 3.1) and, for PDDS_COEF_TABLE, padded device copies
  * of the coefficient tables with their TMA descriptors.  Synchronizes the
- * device.  Errors: EINVAL (grid/coeffs), ENOMEM, ECUDA. */
+ * device.  Errors: EINVAL (grid/coeffs; also a potential c > 0 anywhere: the
+ * paper's setting takes c <= 0, and the path weights Y = exp(int c dt) <= 1
+ * are summed as exact 2^-30 fixed point), ENOMEM, ECUDA. */
 pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* coeffs, pdds_ctx** out);
 void pdds_destroy(pdds_ctx* ctx);
 
@@ -170,11 +173,26 @@ pdds_status pdds_get_launch(const pdds_ctx* ctx, int32_t* block, int32_t* ctas_p
 pdds_status pdds_autotune(pdds_ctx* ctx, int64_t n_paths, double dt, uint64_t seed,
                           void* cuda_stream);
 
+/* Philox tag of the single-problem calls on ctx (pdds_assemble,
+ * pdds_assemble_records, pdds_assemble_solve_host, pdds_calibrate,
+ * pdds_autotune): the fourth counter word of every path's stream, (q, p, k,
+ * tag).  Default 0.  pdds_assemble_batch gives problem i the tag i whatever
+ * this setting, so a single-problem call with tag i on the context of problem
+ * i draws the same Gaussians as that problem does in a batch (used to check a
+ * batch row by row with per-path records).  Applies to later calls. */
+pdds_status pdds_set_philox_tag(pdds_ctx* ctx, uint32_t tag);
+
 /* Bound, in seconds, on every device-side wait of the path kernel (a warp
- * waiting for the next work unit of its CTA).  When a wait runs out the kernel
- * stops taking work, returns, and pdds_stats reports PDDS_ETIMEOUT; the
- * results of that call are then incomplete.  0 restores the default:
- * 10 s plus 4 us per step of the step cap. */
+ * waiting for the next work unit of its CTA, or for the TMA copy of a
+ * tabulated-coefficient tile).  When a wait runs out the kernel stops taking
+ * work, returns, and pdds_stats reports PDDS_ETIMEOUT; the results of that
+ * call (G, b, records, counters) are then incomplete and must be discarded.
+ * What a timeout leaves behind: nothing on the device beyond those partial
+ * results (no memory, no pending work); a tile copy that had not landed when
+ * its wait ran out is given a further max(limit, 1 s) to land before its CTA
+ * returns, so that no copy is left writing into released shared memory.
+ * The context stays usable.  0 restores the default: 10 s plus 4 us per step
+ * of the step cap (40 us per step with the in-path network). */
 pdds_status pdds_set_wait_limit(pdds_ctx* ctx, double seconds);
 
 /* When on, the path kernel is bracketed by CUDA events on the caller's stream
@@ -382,7 +400,10 @@ pdds_status pdds_set_control_variate_grid(pdds_ctx* ctx, const float* grad_xy, i
  *   G->n must be in [1, 131072]; larger systems are rejected with PDDS_EINVAL
  *     before any device work (use pdds_solve).
  * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  The address
+ * is kept for the life of the process: after a cudaDeviceReset (or any other
+ * teardown of the device's primary context) it is stale, so a process that
+ * resets a device must not call pdds_solve_noalloc on that device again.  All calls
  * in the process share the one array per device: calls that overlap on the
  * GPU (other host threads or other streams) race and corrupt each other's
  * results -- serialize them.  Each call re-initialises every part of the array
@@ -400,6 +421,28 @@ pdds_status pdds_assemble_solve_host(pdds_ctx* ctx, const int64_t* n_per_knot_ho
                                      int32_t maxit, int32_t* row_ptr_host, int32_t* col_host,
                                      double* val_host, double* b_host, double* u_host,
                                      void* cuda_stream);
+
+/* End-to-end batch with HOST buffers: the `count` problems of
+ * pdds_assemble_batch in ONE persistent launch (replayed from its CUDA graph),
+ * then each problem's FP64 BiCGSTAB solve (Eq. 23), all on the device.  Per
+ * call: the per-knot budgets go up (n_per_knot_host[i]: int64[n_i], or NULL /
+ * a NULL array for n_paths everywhere) and G (row_ptr[n_i+1], col[nnz_i],
+ * val[nnz_i]), b[n_i] and u[n_i] of every problem come down.  Every array has
+ * `count` entries of HOST pointers (pinned memory copies fastest); row_ptr_host
+ * and col_host (or their entries) may be NULL to skip the pattern, val, b and
+ * u may not.  Device buffers are each context's own scratch (allocated on the
+ * first call and kept).  Budgets outside [0, 2^31) are rejected (EINVAL)
+ * before any copy or launch.  Restrictions and counters as for
+ * pdds_assemble_batch (the launch's counters and time are read with
+ * pdds_stats(ctxs[0]); its kernel_launches then counts the batch and all
+ * solves).  Returns ENOCONV if some solve did not reach rtol (every result is
+ * still copied back).  Synchronizes the stream. */
+pdds_status pdds_assemble_solve_batch_host(pdds_ctx* const* ctxs, int32_t count,
+                                           const int64_t* const* n_per_knot_host, int64_t n_paths,
+                                           double dt, uint64_t seed, double rtol, int32_t maxit,
+                                           int32_t* const* row_ptr_host, int32_t* const* col_host,
+                                           double* const* val_host, double* const* b_host,
+                                           double* const* u_host, void* cuda_stream);
 
 /* Counters of the last assemble / solve (synchronizes the device).  Returns
  * the device error the last assembly recorded (out->device_error: PDDS_ETIMEOUT

@@ -605,18 +605,23 @@ __device__ bool load_unit(const Smem& S, int s, int q, const KParams& P, int64_t
       tma_load_2d(S.tile(s, 0), D.tmap, 2 * H.kd.tile_i0, H.kd.tile_j0, &H.mbar);
     }
     __syncwarp();
+    // The wait is bounded by the launch's wait limit (pdds_set_wait_limit).
     const int parity = H.tma_phase;
     const uint64_t t0 = global_ns();
     bool ok = true;
     while (!mbar_try_wait(&H.mbar, parity)) {
-      if (global_ns() - t0 > 2000000000ull) { ok = false; break; }
+      if (global_ns() - t0 > P.wait_ns) { ok = false; break; }
     }
     ok = __all_sync(kFull, ok);
     if (!ok) {
       if (lane == 0) atomicExch(&P.scratch->error, (int)PDDS_ETIMEOUT);
-      // give the copy in flight a second bounded chance to land before leaving
+      // Before the CTA leaves, the copy in flight gets a second bounded wait
+      // of at least one second, however short the limit: a copy that landed
+      // after the CTA had left would write into shared memory it no longer
+      // owns.  The error recorded above voids the call's results.
+      const uint64_t drain = P.wait_ns > 1000000000ull ? P.wait_ns : 1000000000ull;
       const uint64_t t1 = global_ns();
-      while (!mbar_try_wait(&H.mbar, parity) && global_ns() - t1 < 2000000000ull) {
+      while (!mbar_try_wait(&H.mbar, parity) && global_ns() - t1 < drain) {
       }
       return false;
     }

@@ -223,6 +223,7 @@ struct pdds_ctx {
   int block = 256, ctas_per_sm = 0, exit_batch = 4;
   int64_t unit_paths = 4096;
   int64_t k_max = 0;
+  uint32_t tag = 0;  // Philox tag (fourth counter word) of single-problem calls
   bool timing = false;
   bool timing_pending = false;  // ev0/ev1 recorded around a path kernel, time not read yet
   double wait_s = 0;
@@ -482,7 +483,7 @@ pdds_status assemble_impl(pdds_ctx* c, const int64_t* N, int64_t Nu, double dt, 
   CK(c, cudaMemsetAsync(G->val, 0, c->geo.nnz * 8, s));
   CK(c, cudaMemsetAsync(b, 0, c->geo.n * 8, s));
   CK(c, cudaMemsetAsync(c->d_scratch, 0, sizeof(pdds::Scratch), s));
-  ProbDesc D = make_prob(c, 0);
+  ProbDesc D = make_prob(c, (int)c->tag);
   D.Gval = G->val;
   D.b = b;
   D.n_per_knot = N;
@@ -555,6 +556,12 @@ pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx**
     free_ctx(c);
     return fail(nullptr, PDDS_EINVAL, err);
   }
+  // c <= 0 (the setting of Eq. 6): the weight Y = exp(int c dt) stays <= 1,
+  // which the exact 2^-30 fixed-point slot sums of the path kernel rely on
+  if (c->coef_id == PDDS_COEF_CONSTANT && !(cf->params[3] <= 0)) {
+    free_ctx(c);
+    return fail(nullptr, PDDS_EINVAL, "create: CONSTANT needs params[3] (c) <= 0");
+  }
   if (c->coef_id == PDDS_COEF_CONSTANT && !(std::fabs(cf->params[0]) > 0)) {
     free_ctx(c);
     return fail(nullptr, PDDS_EINVAL, "create: CONSTANT needs params[0] (sigma) != 0");
@@ -585,6 +592,16 @@ pdds_status pdds_create(const pdds_grid* grid, const pdds_coeffs* cf, pdds_ctx**
       return bail(e, "sigma table copy");
     if ((e = cudaMemcpy(c_host.data(), cf->c_tab, cnt * 4, cudaMemcpyDefault)) != cudaSuccess)
       return bail(e, "c table copy");
+    for (size_t i = 0; i < cnt; ++i) {
+      // c <= 0 keeps Y <= 1 (exact fixed-point slot sums); s finite and nonzero
+      if (!(c_host[i] <= 0.0f) || !std::isfinite(c_host[i]) || !std::isfinite(sig_host[i]) ||
+          sig_host[i] == 0.0f) {
+        free_ctx(c);
+        return fail(nullptr, PDDS_EINVAL,
+                    "create: TABLE needs every c_tab value finite and <= 0 and every sigma_tab "
+                    "value finite and nonzero");
+      }
+    }
     // Tile covering every patch: nodes [i0, i0 + w) x [j0, j0 + h) with i0 a
     // multiple of 4 (16-byte TMA inner coordinate).
     const double tdx = (grid->x1 - grid->x0) / (cf->tab_nx - 1);
@@ -744,6 +761,12 @@ pdds_status pdds_get_launch(const pdds_ctx* c, int32_t* block, int32_t* per_sm,
   if (per_sm) *per_sm = c->ctas_per_sm;
   if (unit_paths) *unit_paths = (int32_t)c->unit_paths;
   if (exit_batch) *exit_batch = c->exit_batch;
+  return PDDS_OK;
+}
+
+pdds_status pdds_set_philox_tag(pdds_ctx* c, uint32_t tag) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_philox_tag: NULL context");
+  c->tag = tag;
   return PDDS_OK;
 }
 
@@ -1139,11 +1162,9 @@ pdds_status pdds_solve(pdds_ctx* c, const pdds_csr* G, const double* b, double* 
   c->st.kernel_launches += nl;
   if (iters) *iters = it;
   if (conv != 1) {
-    static const char* why[] = {"", " ((rh,v) = 0)", " (omega = 0)", " ((rh,r) = 0)",
-                                " (residual not finite)"};
     char buf[200];
     std::snprintf(buf, sizeof buf, "solve: no convergence after %d iterations (relres %.3e)%s",
-                  it, rel, (conv < 0 && -conv <= 4) ? why[-conv] : "");
+                  it, rel, pdds::bicgstab_stop_reason(conv));
     return fail(c, PDDS_ENOCONV, buf);
   }
   return PDDS_OK;
@@ -1336,6 +1357,82 @@ pdds_status pdds_assemble_batch(pdds_ctx* const* ctxs, int32_t count,
   for (int i = 0; i < count; ++i) launches += (N && N[i]) ? 1 : 0;
   c0->st.kernel_launches = launches;
   return PDDS_OK;
+}
+
+pdds_status pdds_assemble_solve_batch_host(pdds_ctx* const* ctxs, int32_t count,
+                                           const int64_t* const* N_host, int64_t Nu, double dt,
+                                           uint64_t seed, double rtol, int32_t maxit,
+                                           int32_t* const* rp_host, int32_t* const* col_host,
+                                           double* const* val_host, double* const* b_host,
+                                           double* const* u_host, void* stream) {
+  if (!ctxs || count < 1 || !ctxs[0])
+    return fail(nullptr, PDDS_EINVAL, "assemble_solve_batch_host: need count >= 1 contexts");
+  pdds_ctx* c0 = ctxs[0];
+  if (!val_host || !b_host || !u_host)
+    return fail(c0, PDDS_EINVAL,
+                "assemble_solve_batch_host: val, b and u host pointer arrays are required");
+  for (int i = 0; i < count; ++i) {
+    pdds_ctx* c = ctxs[i];
+    if (!c) return fail(c0, PDDS_EINVAL, "assemble_solve_batch_host: NULL context in the list");
+    if (!val_host[i] || !b_host[i] || !u_host[i])
+      return fail(c0, PDDS_EINVAL, "assemble_solve_batch_host: NULL val, b or u host buffer");
+    const int64_t* Nh = N_host ? N_host[i] : nullptr;
+    for (int64_t k = 0; Nh && k < c->geo.n; ++k)
+      if (Nh[k] < 0 || Nh[k] > 0x7fffffffll)
+        return fail(c0, PDDS_EINVAL, "assemble_solve_batch_host: every N_k must be in [0, 2^31)");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // Device buffers: each context's own end-to-end scratch (kept for reuse).
+  std::vector<pdds_csr> Gs(count);
+  std::vector<pdds_csr*> Gp(count);
+  std::vector<double*> bd(count);
+  std::vector<const int64_t*> Nd(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    pdds_ctx* c = ctxs[i];
+    const int64_t n = c->geo.n, nnz = c->geo.nnz;
+    if (!c->e_rp) {
+      CK(c0, dalloc(&c->e_N, n));
+      CK(c0, dalloc(&c->e_rp, n + 1));
+      CK(c0, dalloc(&c->e_col, nnz));
+      CK(c0, dalloc(&c->e_val, nnz));
+      CK(c0, dalloc(&c->e_b, n));
+      CK(c0, dalloc(&c->e_u, n));
+    }
+    if (N_host && N_host[i]) {
+      CK(c0, cudaMemcpyAsync(c->e_N, N_host[i], n * 8, cudaMemcpyHostToDevice, s));
+      Nd[i] = c->e_N;
+    }
+    Gs[i] = pdds_csr{n, nnz, c->e_rp, c->e_col, c->e_val};
+    Gp[i] = &Gs[i];
+    bd[i] = c->e_b;
+  }
+  if (pdds_status e = pdds_assemble_batch(ctxs, count, N_host ? Nd.data() : nullptr, Nu, dt, seed,
+                                          Gp.data(), bd.data(), stream))
+    return e;
+  pdds_status worst = PDDS_OK;
+  int launches = c0->st.kernel_launches;
+  for (int i = 0; i < count; ++i) {
+    pdds_ctx* c = ctxs[i];
+    const int before = c->st.kernel_launches;
+    pdds_status se = pdds_solve(c, &Gs[i], c->e_b, c->e_u, rtol, maxit, nullptr, stream);
+    if (se != PDDS_OK && se != PDDS_ENOCONV) return c == c0 ? se : fail(c0, se, c->err);
+    if (se == PDDS_ENOCONV) worst = PDDS_ENOCONV;
+    launches += c->st.kernel_launches - before;
+  }
+  for (int i = 0; i < count; ++i) {
+    pdds_ctx* c = ctxs[i];
+    const int64_t n = c->geo.n, nnz = c->geo.nnz;
+    if (rp_host && rp_host[i])
+      CK(c0, cudaMemcpyAsync(rp_host[i], c->e_rp, (n + 1) * 4, cudaMemcpyDeviceToHost, s));
+    if (col_host && col_host[i])
+      CK(c0, cudaMemcpyAsync(col_host[i], c->e_col, nnz * 4, cudaMemcpyDeviceToHost, s));
+    CK(c0, cudaMemcpyAsync(val_host[i], c->e_val, nnz * 8, cudaMemcpyDeviceToHost, s));
+    CK(c0, cudaMemcpyAsync(b_host[i], c->e_b, n * 8, cudaMemcpyDeviceToHost, s));
+    CK(c0, cudaMemcpyAsync(u_host[i], c->e_u, n * 8, cudaMemcpyDeviceToHost, s));
+  }
+  CK(c0, cudaStreamSynchronize(s));
+  c0->st.kernel_launches = launches;
+  return worst;
 }
 
 }  // extern "C"

@@ -181,5 +181,12 @@ cudaError_t bicgstab_device(const int32_t* row_ptr, const int32_t* col, const do
 size_t bicgstab_work_doubles(int64_t n);
 void set_global_error(const std::string& msg);  // text of pdds_last_error(NULL)
 size_t bicgstab_scalars_bytes();
+// Why a BiCGSTAB run stopped without converging, from the `converged` output
+// of bicgstab_device (negative: a breakdown of the recurrence; 0: maxit).
+inline const char* bicgstab_stop_reason(int converged) {
+  static const char* why[] = {"", " ((rh,v) = 0)", " (omega = 0)", " ((rh,r) = 0)",
+                              " (residual not finite)"};
+  return (converged < 0 && -converged <= 4) ? why[-converged] : "";
+}
 
 }  // namespace pdds

@@ -314,9 +314,10 @@ extern "C" pdds_status pdds_solve_noalloc(const pdds_csr* G, const double* b, do
   }
   if (iters) *iters = it;
   if (conv != 1) {
-    char buf[160];
-    std::snprintf(buf, sizeof buf, "solve_noalloc: no convergence after %d iterations (relres %.3e)",
-                  it, rel);
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "solve_noalloc: no convergence after %d iterations (relres %.3e)%s", it, rel,
+                  bicgstab_stop_reason(conv));
     set_global_error(buf);
     return PDDS_ENOCONV;
   }

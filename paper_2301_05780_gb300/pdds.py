@@ -77,6 +77,7 @@ _SIGS = {
     "pdds_get_launch": (C.c_int, [_P, _P, _P, _P, _P]),
     "pdds_set_timing": (C.c_int, [_P, C.c_int32]),
     "pdds_set_wait_limit": (C.c_int, [_P, C.c_double]),
+    "pdds_set_philox_tag": (C.c_int, [_P, C.c_uint32]),
     "pdds_autotune": (C.c_int, [_P, C.c_int64, C.c_double, C.c_uint64, _P]),
     "pdds_assemble": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P]),
     "pdds_assemble_records": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P,
@@ -98,6 +99,9 @@ _SIGS = {
     "pdds_set_control_variate_grid": (C.c_int, [_P, _P, C.c_int32, C.c_int32]),
     "pdds_assemble_solve_host": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_double,
                                            C.c_int32, _P, _P, _P, _P, _P, _P]),
+    "pdds_assemble_solve_batch_host": (C.c_int, [_P, C.c_int32, _P, C.c_int64, C.c_double,
+                                                 C.c_uint64, C.c_double, C.c_int32, _P, _P, _P,
+                                                 _P, _P, _P]),
     "pdds_stats": (C.c_int, [_P, _P]),
     "pdds_last_error": (C.c_char_p, [_P]),
 }
@@ -214,6 +218,12 @@ def pdds_autotune(ctx, n_paths, dt, seed=0, stream=None):
 
 def pdds_set_wait_limit(ctx, seconds: float):
     _check(lib().pdds_set_wait_limit(ctx, float(seconds)), ctx)
+
+
+def pdds_set_philox_tag(ctx, tag: int):
+    """Philox tag of later single-problem calls on ctx (problem i of a batch
+    draws with tag i)."""
+    _check(lib().pdds_set_philox_tag(ctx, C.c_uint32(int(tag))), ctx)
 
 
 def pdds_set_timing(ctx, on: bool):
@@ -387,6 +397,32 @@ def pdds_assemble_solve_host(ctx, n_paths, dt, seed, rtol, maxit, row_ptr, col, 
                                         _stream(stream))
     if st not in (PDDS_OK, PDDS_ENOCONV):
         _check(st, ctx)
+    return st
+
+
+def pdds_assemble_solve_batch_host(ctxs, n_paths, dt, seed, rtol, maxit, row_ptr, col, val, b,
+                                   u, n_per_knot=None, stream=None):
+    """Host-buffer batch: lists (one entry per problem) of host arrays (numpy
+    or pinned torch CPU tensors); row_ptr / col / n_per_knot may be None."""
+    count = len(ctxs)
+
+    def ptr(a):
+        if a is None:
+            return None
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    def arr(lst):
+        if lst is None:
+            return None
+        return (C.c_void_p * count)(*[ptr(a) for a in lst])
+
+    carr = (C.c_void_p * count)(*[c.value for c in ctxs])
+    st = lib().pdds_assemble_solve_batch_host(carr, count, arr(n_per_knot), int(n_paths),
+                                              float(dt), C.c_uint64(int(seed) % 2**64),
+                                              float(rtol), int(maxit), arr(row_ptr), arr(col),
+                                              arr(val), arr(b), arr(u), _stream(stream))
+    if st not in (PDDS_OK, PDDS_ENOCONV):
+        _check(st, ctxs[0])
     return st
 
 

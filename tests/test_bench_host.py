@@ -93,3 +93,19 @@ def test_reference_arm_prints_its_line():
     assert line["e2e"] == {"value": line["value"], "unit": "path-steps/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "cfg1_laplace_2x2"
+
+
+def test_reference_arm_default_is_the_batched_workload():
+    """With no --config the reference arm times the oracle on the default
+    workload, the 16-problem batch (config 3), on a bounded sample per step."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                          "reference", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["workload"] == "cfg3_batch16"
+    assert line["value"] > 0 and line["steps"] == 1
+    assert 0 < line["config"]["sample_budget_fraction"] <= 1
+    assert "16 problems" in line["cpu_baseline"]["sample"]

@@ -196,7 +196,7 @@ def _moments(pe, pg, x, idx, n):
 @pytest.mark.parametrize("use_cv,k_cap,knot_steps", [
     (False, None, False), (True, None, False), (False, 60, False), (False, None, True),
     ("table", None, False)])
-def test_calibration_moments_parity(orc, use_cv, k_cap, knot_steps):
+def test_calibration_moments_parity(orc, oracle_theta, use_cv, k_cap, knot_steps):
     """pdds_calibrate against the oracle's mixed GM/EM run on the same streams
     and the same u0: flagged paths (step count or side differing in either
     exit) removed by each side; moments agree to the FP32 path rounding (and
@@ -220,13 +220,9 @@ def test_calibration_moments_parity(orc, use_cv, k_cap, knot_steps):
                         -np.pi * np.sin(np.pi * X) * np.sin(np.pi * Y) + X],
                        axis=-1).astype(np.float32)
     elif use_cv:
-        th = torch.tensor(W.mlp_init(), dtype=torch.float32, device="cuda")
-        rng = np.random.default_rng(13)
-        xy = rng.uniform(0, 1, size=(4096, 2))
-        tgt = np.sin(np.pi * xy[:, 0]) * np.cos(np.pi * xy[:, 1]) + xy[:, 0] * xy[:, 1]
-        pdds.pdds_mlp_train(th, torch.tensor(xy, dtype=torch.float32, device="cuda"),
-                            torch.tensor(tgt, dtype=torch.float32, device="cuda"), steps=400)
-        theta = th
+        # a network fitted by the oracle itself: nothing the oracle reads comes
+        # from the library
+        theta = torch.tensor(oracle_theta, dtype=torch.float32, device="cuda")
     # GPU: calibration moments, plus the two record passes it is made of
     P = _problem(w, EM, h_per_knot=h_k, theta=theta)
     if tab is not None:

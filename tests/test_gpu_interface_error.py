@@ -7,9 +7,10 @@ Two figures per workload:
     oracle finishes in seconds: both sides draw the same Gaussians, so the
     difference is the FP32 path arithmetic alone (the rare exit decisions
     that flip near a side, and the rounding of the weights).
-Each test prints its figures on one line beginning "u-error".  The bounds
-are about ten times the figures measured on a GB300 (the runs are seeded, so
-they move only if the FP32 rounding of the paths changes).
+Each test prints its figures on one line beginning "u-error".  Against the
+oracle u is bounded both in RMS and knot by knot (max over the knots).  The
+bounds are about ten times the figures measured on a GB300 (the runs are
+seeded, so they move only if the FP32 rounding of the paths changes).
 """
 import math
 
@@ -59,7 +60,7 @@ def oracle_u(orc, w, n_paths, tag=0):
     return u, O.xy
 
 
-def check_single(orc, w, n_oracle, tol_exact, tol_oracle):
+def check_single(orc, w, n_oracle, tol_exact, tol_oracle, tol_oracle_max):
     line = [f"u-error {w.name}"]
     if tol_exact is not None:
         u, xy = gpu_u(w)
@@ -76,22 +77,23 @@ def check_single(orc, w, n_oracle, tol_exact, tol_oracle):
     line.append(f"vs oracle {d:.3e} (max {np.abs(ug - uo).max():.3e}) at N={n_oracle}")
     print("; ".join(line))
     assert d < tol_oracle
+    assert np.abs(ug - uo).max() < tol_oracle_max     # knot by knot, not only in the mean
 
 
 def test_config1_u_error(orc):
-    check_single(orc, W.config1(), 10_000, 2e-2, 2e-5)
+    check_single(orc, W.config1(), 10_000, 2e-2, 2e-5, 1e-4)
 
 
 def test_config2_u_error(orc):
-    check_single(orc, W.config2(), 2000, 2e-2, 1e-5)
+    check_single(orc, W.config2(), 2000, 2e-2, 1e-5, 2e-4)
 
 
 def test_config4_u_error(orc):
-    check_single(orc, W.config4(), 30, None, 1e-5)
+    check_single(orc, W.config4(), 30, None, 1e-5, 1e-3)
 
 
 def test_config5_u_error(orc):
-    check_single(orc, W.config5(), 500, 5e-2, 1e-4)
+    check_single(orc, W.config5(), 500, 5e-2, 1e-4, 1e-3)
 
 
 def test_config3_u_error(orc):
@@ -130,3 +132,4 @@ def test_config3_u_error(orc):
           f"(max {np.abs(d).max():.3e}) at budgets clamped to {cap}")
     assert rms(err) < 1e-2
     assert rms(d) < 1e-4
+    assert np.abs(d).max() < 5e-3                       # knot by knot

@@ -251,7 +251,10 @@ def test_config4_sampled_rows(orc):
 # ------------------------------------------------------------------ batch
 def test_batch_one_launch_matches_oracle(orc):
     """Three problems (different grids) in one persistent launch: problem i
-    uses Philox tag i; sampled rows of each against the oracle with that tag."""
+    uses Philox tag i.  Each problem's sampled rows equal, to FP64 summation
+    order, a single-problem records launch with tag i in which only those rows
+    get paths, and that launch goes against the oracle (tag i) with flagged
+    paths removed."""
     ws = W.config3()[:3]
     probs = [pdds.Problem(w) for w in ws]
     for P, w in zip(probs, ws):
@@ -263,64 +266,24 @@ def test_batch_one_launch_matches_oracle(orc):
     assert pdds.pdds_stats(probs[0].ctx)["device_error"] == 0
     for i, (P, w) in enumerate(zip(probs, ws)):
         Nk = P.n_per_knot.cpu().numpy()
+        bv, bb = P.val.cpu().numpy(), P.b.cpu().numpy()
         rows = np.array([0, P.n // 2, P.n - 1], dtype=np.int32)
-        O = orc.Problem(w.grid, w.coef_id, w.params)
-        val, b, _, _ = O.assemble(Nk, w.dt, w.seed, w.k_max, rows=rows, tag=i)
-        gv, gb = P.val.cpu().numpy(), P.b.cpu().numpy()
+        mask = np.zeros_like(Nk)
+        mask[rows] = Nk[rows]
+        pdds.pdds_set_philox_tag(P.ctx, i)
+        P.n_per_knot = torch.from_numpy(mask).cuda()
+        rec = P.records_buffer()
+        P.assemble(records=rec)
+        torch.cuda.synchronize()
+        assert pdds.pdds_stats(P.ctx)["device_error"] == 0
+        g = dict(row_ptr=P.row_ptr.cpu().numpy(), col=P.col.cpu().numpy(),
+                 val=P.val.cpu().numpy(), b=P.b.cpu().numpy(), rec=pdds.records_to_numpy(rec))
         for k in rows:
-            s, e = O.row_ptr[k], O.row_ptr[k + 1]
-            # without records, allow up to four flipped paths per row (each moves
-            # an entry by at most 1/N_k and b_k by at most max|g|/N_k ~ 3/N_k)
-            assert np.abs(gv[s:e] - val[s:e]).max() < 4.0 / Nk[k] + 1e-9, (i, k)
-            assert abs(gb[k] - b[k]) < 12.0 / Nk[k] + 1e-9, (i, k)
-
-
-def test_config3_full_batch_sampled_rows(orc):
-    """All 16 config-3 problems at their full per-knot budgets in one batched
-    launch, as the benchmark runs them.  Problem 0 (Philox tag 0): its sampled
-    rows equal, to FP64 summation order, a single-problem launch with records
-    in which only those rows get paths (a path's counters depend on its step,
-    index, knot and tag only), and that launch goes against the oracle with
-    flagged paths removed.  Four small-patch problems (tags 3, 6, 13, 14):
-    sampled rows against the oracle within four flipped paths per row."""
-    ws = W.config3()
-    probs = [pdds.Problem(w) for w in ws]
-    pdds.pdds_assemble_batch([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs],
-                             0, [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
-    torch.cuda.synchronize()
-    assert pdds.pdds_stats(probs[0].ctx)["device_error"] == 0
-    # problem 0: batch == masked single launch (records) == oracle
-    w0, P0 = ws[0], probs[0]
-    Nk0 = P0.n_per_knot.cpu().numpy()
-    order = np.argsort(Nk0, kind="stable")
-    rows0 = np.sort(np.concatenate([order[:7], order[-1:]])).astype(np.int32)
-    mask = np.zeros_like(Nk0)
-    mask[rows0] = Nk0[rows0]
-    g = run_gpu(w0, records=True, n_per_knot=mask)
-    bv, bb = P0.val.cpu().numpy(), P0.b.cpu().numpy()
-    for k in rows0:
-        s_, e_ = g["row_ptr"][k], g["row_ptr"][k + 1]
-        assert np.allclose(bv[s_:e_], g["val"][s_:e_], rtol=1e-11, atol=1e-14), k
-        assert np.isclose(bb[k], g["b"][k], rtol=1e-11, atol=1e-14), k
-    o = run_oracle(orc, w0, rows=rows0, n_per_knot=Nk0)
-    g_rows = dict(g)
-    g_rows["rec"] = gpu_rows_records(g, rows0, mask)
-    parity.compare_rows(g_rows, o, rows0, Nk0[rows0], len(Nk0))
-    # other problems, their own tags
-    for i in (3, 6, 13, 14):
-        w, P = ws[i], probs[i]
-        Nk = P.n_per_knot.cpu().numpy()
-        order = np.argsort(Nk, kind="stable")
-        rows = np.sort(np.concatenate([order[:2], order[-1:]])).astype(np.int32)
-        O = orc.Problem(w.grid, w.coef_id, w.params)
-        val, b, _, _ = O.assemble(Nk, w.dt, w.seed, w.k_max, rows=rows, tag=i)
-        gv, gb = P.val.cpu().numpy(), P.b.cpu().numpy()
-        for k in rows:
-            s_, e_ = O.row_ptr[k], O.row_ptr[k + 1]
-            assert np.abs(gv[s_:e_] - val[s_:e_]).max() < 4.0 / Nk[k] + 1e-9, (i, k)
-            assert abs(gb[k] - b[k]) < 12.0 / Nk[k] + 1e-9, (i, k)
-    for P in probs:
-        P.close()
+            s_, e_ = g["row_ptr"][k], g["row_ptr"][k + 1]
+            assert np.allclose(bv[s_:e_], g["val"][s_:e_], rtol=1e-11, atol=1e-14), (i, k)
+            assert np.isclose(bb[k], g["b"][k], rtol=1e-11, atol=1e-14), (i, k)
+        o = run_oracle(orc, w, rows=rows, n_per_knot=Nk, tag=i)
+        parity.compare_rows(g, o, rows, Nk[rows], P.n)
 
 
 def test_batch_replay_is_deterministic_in_structure():
@@ -337,6 +300,45 @@ def test_batch_replay_is_deterministic_in_structure():
     torch.cuda.synchronize()
     for P, v in zip(probs, first):
         assert torch.allclose(P.val, v, rtol=1e-11, atol=1e-14)
+
+
+def test_batch_host_buffers_match_device_calls():
+    """pdds_assemble_solve_batch_host (budgets up, G, b, u of every problem
+    down) gives the batched device call's G and b and the per-problem solves'
+    u on the same streams, to FP64 summation order; a budget outside
+    [0, 2^31) is rejected before any launch."""
+    ws = W.config3()[2:5]
+    probs = [pdds.Problem(w) for w in ws]
+    for P, w in zip(probs, ws):
+        P.n_per_knot = torch.from_numpy(np.minimum(w.budgets(P.n), 700)).cuda()
+    pdds.pdds_assemble_batch([P.ctx for P in probs], [P.G for P in probs], [P.b for P in probs],
+                             0, [P.n_per_knot for P in probs], ws[0].dt, ws[0].seed)
+    for P in probs:
+        P.solve(rtol=1e-12)
+    torch.cuda.synchronize()
+    Nh = [P.n_per_knot.cpu().numpy() for P in probs]
+    rp = [np.zeros(P.n + 1, np.int32) for P in probs]
+    col = [np.zeros(P.nnz, np.int32) for P in probs]
+    val = [np.zeros(P.nnz) for P in probs]
+    b = [np.zeros(P.n) for P in probs]
+    u = [np.zeros(P.n) for P in probs]
+    st = pdds.pdds_assemble_solve_batch_host([P.ctx for P in probs], 0, ws[0].dt, ws[0].seed,
+                                             1e-12, 5000, rp, col, val, b, u, n_per_knot=Nh)
+    assert st == pdds.PDDS_OK
+    stats = pdds.pdds_stats(probs[0].ctx)
+    assert stats["device_error"] == 0 and stats["paths"] == sum(int(x.sum()) for x in Nh)
+    for i, P in enumerate(probs):
+        assert np.array_equal(rp[i], P.row_ptr.cpu().numpy())
+        assert np.array_equal(col[i], P.col.cpu().numpy())
+        assert np.allclose(val[i], P.val.cpu().numpy(), rtol=1e-11, atol=1e-14)
+        assert np.allclose(b[i], P.b.cpu().numpy(), rtol=1e-11, atol=1e-14)
+        assert np.allclose(u[i], P.u.cpu().numpy(), rtol=1e-8, atol=1e-11)
+    bad = [x.copy() for x in Nh]
+    bad[1][0] = 2 ** 31
+    with pytest.raises(pdds.PddsError) as e:
+        pdds.pdds_assemble_solve_batch_host([P.ctx for P in probs], 0, ws[0].dt, ws[0].seed,
+                                            1e-12, 5000, rp, col, val, b, u, n_per_knot=bad)
+    assert e.value.status == pdds.PDDS_EINVAL
 
 
 # ------------------------------------------------------------------ solve

@@ -157,3 +157,52 @@ def test_stencils_collinear_gapfree(orc):
             if 0 < line_y < L:
                 expect |= {(t, line_y) for t in range(max(ilo - ext, 1), min(ihi + ext, L - 1) + 1)}
         assert pts == expect, k
+
+
+_TRITON_PHILOX = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"   # run the kernel on the CPU
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def _philox(c0p, c1p, c2p, c3p, k0p, k1p, out, n: tl.constexpr):
+    i = tl.arange(0, n)
+    a, b, c, d = tl.philox_impl(tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i),
+                                tl.load(c3p + i), tl.load(k0p + i), tl.load(k1p + i), 10)
+    tl.store(out + 4 * i, a)
+    tl.store(out + 4 * i + 1, b)
+    tl.store(out + 4 * i + 2, c)
+    tl.store(out + 4 * i + 3, d)
+
+x = np.array(json.loads(sys.stdin.read()), dtype=np.int64)   # rows: c0 c1 c2 c3 k0 k1
+n = x.shape[0]
+col = [torch.tensor(x[:, j].astype(np.uint32)) for j in range(6)]
+out = torch.zeros(4 * n, dtype=torch.uint32)
+_philox[(1,)](*col, out, n)
+print(json.dumps(out.to(torch.int64).reshape(n, 4).tolist()))
+"""
+
+
+def test_philox_matches_an_independent_library_generator(orc):
+    """Philox4x32-10 is a published definition (Salmon et al., SC'11), and
+    Triton ships its own implementation (`triton.language.philox_impl`, ten
+    rounds, counter words (c0..c3), key (k0, k1)).  Run on the CPU by Triton's
+    interpreter, it must give the oracle's four output words bit for bit on the
+    all-zero and all-ones counters and keys and on 250 random ones: a wrong
+    multiplier, Weyl constant, round count or word order fails this."""
+    pytest.importorskip("triton")
+    import subprocess
+    import sys
+    rng = np.random.default_rng(123)
+    rows = np.concatenate([np.zeros((1, 6), np.uint64), np.full((1, 6), 2**32 - 1, np.uint64),
+                           rng.integers(0, 2**32, size=(254, 6), dtype=np.uint64)])
+    out = subprocess.run([sys.executable, "-c", _TRITON_PHILOX],
+                         input=json.dumps(rows.astype(np.int64).tolist()), capture_output=True,
+                         text=True, timeout=600)
+    if out.returncode != 0:
+        pytest.skip(f"Triton's CPU interpreter is unavailable: {out.stderr[-300:]}")
+    lib = np.array(json.loads(out.stdout.strip().splitlines()[-1]), dtype=np.uint64)
+    r32 = rows.astype(np.uint32)
+    for i in range(len(r32)):
+        mine = orc.philox(r32[i:i + 1, :4], r32[i, 4:6].copy())
+        assert np.array_equal(mine[0].astype(np.uint64), lib[i]), (i, mine[0], lib[i])
