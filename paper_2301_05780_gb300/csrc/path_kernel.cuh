@@ -137,6 +137,34 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
   z1 = -rho * sn;
 }
 
+// Packed FP32 pairs (Blackwell FFMA2 / FMUL2 / FADD2: one instruction for two
+// independent FP32 operations, each rounded exactly as its scalar form).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Box-Muller on all four words of one Philox call, both pairs at once in
+// packed arithmetic (the same operations as box_muller, so the same values):
+// gA = rho_a (cos, sin) of the angle of r.y, gB likewise from r.z, r.w.  These
+// are the NEGATED normals of box_muller (z = -g), i.e. dW = -sqrt(h) g.
+__device__ __forceinline__ void box_muller4(uint4 r, float2& gA, float2& gB) {
+  const float s32 = 2.3283064365386963e-10f;  // 2^-32
+  const float2 ua = fma2(f2(__uint2float_rn(r.x), __uint2float_rn(r.z)), f2(s32, s32),
+                         f2(0.5f * s32, 0.5f * s32));
+  const float2 l = mul2(f2(-1.38629436111989061f, -1.38629436111989061f),
+                        f2(lg2_approx(ua.x), lg2_approx(ua.y)));  // -2 ln u
+  const float ra = sqrt_approx(l.x), rb = sqrt_approx(l.y);
+  float2 t = f2(__uint_as_float(0x3f800000u | (r.y >> 9)), __uint_as_float(0x3f800000u | (r.w >> 9)));
+  t = add2(add2(t, f2(-1.5f, -1.5f)), f2(5.9604644775390625e-8f, 5.9604644775390625e-8f));
+  t = mul2(f2(kTwoPi, kTwoPi), t);
+  float sa, ca, sb, cb;
+  __sincosf(t.x, &sa, &ca);
+  __sincosf(t.y, &sb, &cb);
+  gA = mul2(f2(ra, ra), f2(ca, sa));
+  gB = mul2(f2(rb, rb), f2(cb, sb));
+}
+
 // sin(2 pi t), cos(2 pi t) for any t (argument reduced to [-1/2, 1/2]).
 __device__ __forceinline__ void sincos_2pi(float t, float& s, float& c) {
   const float r = t - rintf(t);
@@ -361,39 +389,45 @@ __device__ __forceinline__ void coeffs(const Stage& H, const float* tsig, const 
     float sx, cx, sy, cy;
     const float pi = 3.14159265358979324f;
     if (trig_direct) {  // |x|, |y| <= 1 (set on the host): pi x is within [-pi, pi]
-      __sincosf(pi * x, &sx, &cx);
-      __sincosf(pi * y, &sy, &cy);
+      const float2 a = mul2(f2(pi, pi), f2(x, y));
+      __sincosf(a.x, &sx, &cx);
+      __sincosf(a.y, &sy, &cy);
     } else {
       sincos_2pi(0.5f * x, sx, cx);
       sincos_2pi(0.5f * y, sy, cy);
     }
     const float sxcy = sx * cy;
-    const float u = fmaf(x, y, sxcy);
-    const float ux = fmaf(pi * cx, cy, y);
-    const float uy = fmaf(-pi * sx, sy, x);
+    // (u, 1 + x^2), (u_x, u_y) and (2 sin(pi y), -2 sin(pi x)) as packed pairs
+    const float2 u_c = fma2(f2(x, x), f2(y, x), f2(sxcy, 1.0f));
+    const float2 uxy = fma2(mul2(f2(pi, -pi), f2(cx, sx)), f2(cy, sy), f2(y, x));
+    const float2 t2 = mul2(f2(2.0f, -2.0f), f2(sy, sx));
     const float lap = (-2.0f * pi * pi) * sxcy;
     s = 1.41421356237309505f;
-    dx = 2.0f * sy * cy;
-    dy = fmaf(-2.0f * sx, sx, 1.0f);
-    c = -fmaf(x, x, 1.0f);
-    f = fmaf(dx, ux, fmaf(dy, uy, fmaf(c, u, lap)));
+    dx = t2.x * cy;
+    dy = fmaf(t2.y, sx, 1.0f);
+    c = -u_c.y;
+    f = fmaf(dx, uxy.x, fmaf(dy, uxy.y, fmaf(c, u_c.x, lap)));
   } else if constexpr (COEF == PDDS_COEF_VARSIGMA) {
     // s = sqrt2 (1 + 0.3 sin 2 pi x sin 2 pi y), c = -1, u = e^{x/4} cos(y/2),
     // f = (s^2/2)(1/16 - 1/4) u + c u.
     float s1, c1, s2, c2, sh, ch;
     if (trig_direct) {  // |x|, |y| <= 7 (set on the host): angles below 45 rad
-      __sincosf(kTwoPi * x, &s1, &c1);
-      __sincosf(kTwoPi * y, &s2, &c2);
-      __sincosf(0.5f * y, &sh, &ch);
+      const float2 a = mul2(f2(kTwoPi, kTwoPi), f2(x, y));
+      s1 = __sinf(a.x);
+      s2 = __sinf(a.y);
+      ch = __cosf(0.5f * y);
+      (void)c1; (void)c2; (void)sh;
     } else {
       sincos_2pi(x, s1, c1);
       sincos_2pi(y, s2, c2);
       sincos_2pi(y * (0.5f / kTwoPi), sh, ch);
     }
-    s = 1.41421356237309505f * fmaf(0.3f * s1, s2, 1.0f);
-    const float u = __expf(0.25f * x) * ch;
+    // q = s / sqrt2; u = 2^{x log2(e) / 4} cos(y/2); f = -u (1 + (3/16) q^2)
+    const float q = fmaf(0.3f * s1, s2, 1.0f);
+    s = 1.41421356237309505f * q;
+    const float u = ex2_approx(x * 0.360673760222241f) * ch;
     dx = 0.f; dy = 0.f; c = -1.0f;
-    f = fmaf(0.5f * s * s * (-0.1875f), u, -u);
+    f = -u * fmaf(0.1875f * q, q, 1.0f);
   } else if constexpr (COEF == PDDS_COEF_TABLE) {
     const float fx = fmaf(xr, H.tab_inv_dx, H.kd.tab_fx);
     const float fy = fmaf(yr, H.tab_inv_dy, H.kd.tab_fy);
@@ -491,6 +525,192 @@ __device__ __forceinline__ void cv_table_grad(const ProbDesc& D, float x, float 
   const float y0 = fmaf(tx, H.y - H.x, H.x), y1 = fmaf(tx, H.w - H.z, H.z);
   gx = fmaf(ty, x1 - x0, x0);
   gy = fmaf(ty, y1 - y0, y0);
+}
+
+// One Euler-Maruyama step (Eq. 9, Sec. 2.3) of a lane's path, in place:
+//   Z -= f Y h,  S += c h log2(e)  (Y = 2^S),  X += d h + s dW,
+// [CV = 2: xi -= Y s grad u0 . dW (Eq. 37)], with dW = -sqrt(h) g for the
+// packed pair g of box_muller4.  The pairs (Z, S) and (X, Y) are updated with
+// packed FP32 instructions; the values are those of the scalar forms.
+template <int COEF, int CV>
+__device__ __forceinline__ void em_step(const Stage& H, const float* tile, const KParams& P,
+                                        float xk, float yk, float h, float hl2, float sqh,
+                                        float2 g, float& X, float& Y, float& Sx, float& Z,
+                                        float& XI) {
+  const float2 a = add2(f2(xk, yk), f2(X, Y));  // the absolute position
+  float s, ddx, ddy, c, f;
+  coeffs<COEF>(H, tile, tile, a.x, a.y, X, Y, P.trig_direct, s, ddx, ddy, c, f);
+  float Yw = 1.0f;
+  if constexpr (has_c<COEF>()) {
+    Yw = ex2_approx(Sx);
+    const float2 zs = fma2(f2(-f * Yw, c), f2(h, hl2), f2(Z, Sx));  // dZ = -f Y dt, dS = c dt
+    Z = zs.x;
+    Sx = zs.y;
+  } else if constexpr (has_f<COEF>()) {
+    Z = fmaf(-f, h, Z);  // c = 0: Y = 1
+  }
+  const float ssh = s * sqh;
+  if constexpr (CV == 2) {
+    // grad u0 from the table; a control variate never runs batched, so the
+    // table is problem 0's, read from the launch constants
+    float gx, gy;
+    cv_table_grad(P.prob0, a.x, a.y, gx, gy);
+    XI = fmaf(Yw * ssh, fmaf(gx, g.x, gy * g.y), XI);
+  }
+  float2 p = f2(X, Y);
+  if constexpr (has_drift<COEF>()) p = fma2(f2(ddx, ddy), f2(h, h), p);
+  p = fma2(f2(-ssh, -ssh), g, p);
+  X = p.x;
+  Y = p.y;
+}
+
+__device__ __forceinline__ bool outside_box(float X, float Y, float bx0, float bx1, float by0,
+                                            float by1) {
+  return (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+}
+
+// What the resolution of one exited path produces (Eq. 22-25).
+struct ExitResult {
+  double bc = 0.0;          // the path's share of b_k (times N_k)
+  int side = 0, flags = 0;  // exit side; bit 0 step cap, bit 1 along-line clamp
+  float Yk = 1.0f, sl = 0.f, s_line = 0.f;
+  int col_a = -1, col_b = -1;  // RECORD: knots of the two linear weights
+  float wa = 0.f, wb = 0.f;
+  bool rbf_exit = false;  // EXT + RBF stencils: the weights are the warp loop's
+};
+
+// Resolution of one exited path (the corner rule of Sec. 3.3; Eq. 22-25):
+// the exit side is the one of smallest positive overshoot (past the sides
+// moved by the Gobet-Menozzi shift when gmc > 0); an exit on the boundary of
+// Omega adds Y g at the normal projection to b, an exit on an interface
+// deposits Y (1 - lam) and Y lam on the two nearest stencil knots (exact 2^-30
+// fixed point in the stage's slot accumulators; boundary knots of the
+// stencil add their weight times g to b).  gm_rec: a Gobet-Menozzi exit of a
+// mixed run, recorded but not deposited.
+template <int COEF, bool RECORD, int CV, bool EXT>
+__device__ __forceinline__ ExitResult resolve_exit(const Smem& S, const KParams& P, int st,
+                                                   float xk, float yk, float X, float Y,
+                                                   float Sx, float Z, float XI, bool trunc,
+                                                   float bx0, float bx1, float by0, float by1,
+                                                   float gmc, bool gm_rec) {
+  ExitResult E;
+  double& bc = E.bc;
+  int& side = E.side;
+  int& flags = E.flags;
+  float& Yk = E.Yk;
+  float& sl = E.sl;
+  float& s_line = E.s_line;
+  int& col_a = E.col_a;
+  int& col_b = E.col_b;
+  float& wa = E.wa;
+  float& wb = E.wb;
+  bool& rbf_exit = E.rbf_exit;
+  const Stage& H = S.st(st);
+  const KnotDesc& kd = H.kd;
+  unsigned long long* acc = S.acc(st);
+  float ov[4] = {X - bx1, Y - by1, bx0 - X, by0 - Y};
+  if constexpr (EXT && !const_sigma<COEF>()) {
+    // overshoots past each side moved by its own shift (a constant s, or
+    // no shift, gives the lane's moved box, used above)
+    if (gmc > 0.f) {
+      float sh[4];
+      gm_shifts<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk, yk, X, Y, gmc, P.trig_direct,
+                      sh);
+      const float* tb = kd.box;
+      ov[0] = X - (tb[1] - sh[0]);
+      ov[1] = Y - (tb[3] - sh[1]);
+      ov[2] = (tb[0] + sh[2]) - X;
+      ov[3] = (tb[2] + sh[3]) - Y;
+    }
+  }
+  // smallest positive overshoot (ties to the earlier side), else (a path
+  // truncated inside the box) the largest; the running best stays in a
+  // register so the overshoots need no indexed (local-memory) array
+  side = -1;
+  float best = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+    if (ov[o] > 0.f && (side < 0 || ov[o] < best)) { side = o; best = ov[o]; }
+  if (side < 0) {
+    side = 0;
+    best = ov[0];
+#pragma unroll
+    for (int o = 1; o < 4; ++o)
+      if (ov[o] > best) { side = o; best = ov[o]; }
+  }
+  if constexpr (has_c<COEF>()) Yk = ex2_approx(Sx);
+  bc = (double)Z;
+  if constexpr (CV != 0) bc += (double)XI;
+  const bool vertical = (side == 0 || side == 2);
+  flags = trunc ? 1 : 0;
+  if ((kd.dirbits >> side) & 1) {
+    // exit on the boundary of Omega: Y g at the normal projection
+    float along = vertical ? (yk + Y) : (xk + X);
+    along = vertical ? fminf(fmaxf(along, H.y0), H.y1) : fminf(fmaxf(along, H.x0), H.x1);
+    const float line = vertical ? fmaf((float)kd.line[side], H.dx, H.x0)
+                                : fmaf((float)kd.line[side], H.dy, H.y0);
+    bc += (double)Yk * (double)g_value<COEF>(H, vertical ? line : along, vertical ? along : line);
+  } else {
+    // exit on an interface: interpolation on the side's extended stencil
+    const int a = kd.a[side], b = kd.b[side];
+    const int kal = vertical ? kd.kj : kd.ki;
+    sl = (float)(kal - a) + (vertical ? Y * H.inv_dy : X * H.inv_dx);
+    const float smax = (float)(b - a);
+    if (sl < 0.f) { sl = 0.f; flags |= 2; }
+    if (sl > smax) { sl = smax; flags |= 2; }
+    s_line = (float)a + sl;
+    if constexpr (EXT) rbf_exit = prob_desc(P, H.prob).rbf_coef != nullptr;
+    if (!rbf_exit) {
+      // linear: the two nearest stencil knots
+      int t = (int)floorf(sl);
+      if (t >= b - a) t = b - a - 1;
+      const float lam = sl - (float)t;
+      // Y (1 - lam) and Y lam in 2^-30 units: q0 + q1 = qY exactly, so the
+      // path deposits its whole weight Y on the two knots (G 1 = b holds
+      // exactly when c = f = 0 and g = 1).
+      const unsigned long long qY = __float2ull_rn(Yk * kFixedOne);
+      const unsigned long long q1 = __float2ull_rn((Yk * lam) * kFixedOne);
+      const unsigned long long qw[2] = {qY - q1, q1};
+      const int lmax = vertical ? H.LY : H.LX;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int tl = a + t + q;
+        if (tl == 0 || tl == lmax) {
+          const int li = vertical ? kd.line[side] : tl;
+          const int lj = vertical ? tl : kd.line[side];
+          bc += (double)qw[q] * kFixedInv *
+                (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
+                                      fmaf((float)lj, H.dy, H.y0));
+        } else {
+          const int slot = kd.off[side] + t + q;
+          if (!gm_rec) atomicAdd(acc + slot, qw[q]);
+          if constexpr (RECORD) {
+            const ProbDesc& D = prob_desc(P, H.prob);
+            const int c = D.slot2csr[kd.slot_base + slot];
+            const int col = D.col[c];
+            const float wv = (float)((double)qw[q] * kFixedInv);
+            if (q == 0) { col_a = col; wa = wv; }
+            else { col_b = col; wb = wv; }
+          }
+        }
+      }
+    }
+  }
+  return E;
+}
+
+// The per-path record of a resolved exit (knot-major: the record prefix of
+// the knot, then the path index).
+__device__ __forceinline__ void write_record(const Smem& S, const KParams& P, int st, uint32_t kk,
+                                             uint32_t p, int n, const ExitResult& E, float XI,
+                                             bool gm_rec) {
+  const ProbDesc& D = prob_desc(P, S.st(st).prob);
+  const int64_t idx = (D.path_prefix ? D.path_prefix[kk] : (int64_t)kk * D.n_paths) + p;
+  PathRecordDev R;
+  R.steps = n; R.side_flags = E.side | (E.flags << 8); R.col_a = E.col_a; R.col_b = E.col_b;
+  R.w_a = E.wa; R.w_b = E.wb; R.b_contrib = (float)E.bc; R.Y = E.Yk;
+  R.xi = XI; R.s_line = E.s_line;
+  (gm_rec ? P.records_gm : P.records)[idx] = R;
 }
 
 // ------------------------------------------------------------ unit loading
@@ -869,8 +1089,46 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
             if (!exited && n >= kmax) { exited = true; trunc = true; }
           }
         }
+      } else if (!EXT && alive && !exited) {
+        // Two Philox calls (four steps) between exit checks of the warp.  The
+        // two steps of a call are taken without a branch between them: the
+        // second one starts from the first one's result, and is dropped when
+        // the first one left the patch or reached the step cap.
+        const Stage& H = S.st(st);
+        const float* tile = S.tile(st, 0);
+#pragma unroll 1
+        for (int pair = 0; pair < 2 && !exited; ++pair) {
+          const uint4 r = kPhiloxPre ? philox_step((uint32_t)(n >> 1), ph, P.round_keys)
+                            : philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
+          float2 gA, gB;
+          box_muller4(r, gA, gB);
+          float X1 = X, Y1 = Y, S1 = Sx, Z1 = Z, XI1 = XI;
+          em_step<COEF, CV>(H, tile, P, xk, yk, h, hl2, sqh, gA, X1, Y1, S1, Z1, XI1);
+          bool e1 = outside_box(X1, Y1, bx0, bx1, by0, by1);
+          float X2 = X1, Y2 = Y1, S2 = S1, Z2 = Z1, XI2 = XI1;
+          em_step<COEF, CV>(H, tile, P, xk, yk, h, hl2, sqh, gB, X2, Y2, S2, Z2, XI2);
+          bool e2 = outside_box(X2, Y2, bx0, bx1, by0, by1);
+          if constexpr (EXT && !const_sigma<COEF>()) {
+            // the box moved by the largest shift only selects candidates
+            if (e1 && gmc > 0.f) e1 = gm_outside<COEF>(H, tile, tile, xk, yk, X1, Y1, gmc,
+                                                      P.trig_direct);
+            if (e2 && !e1 && gmc > 0.f) e2 = gm_outside<COEF>(H, tile, tile, xk, yk, X2, Y2, gmc,
+                                                               P.trig_direct);
+          }
+          const bool first = e1 || (n + 1 >= kmax);
+          X = first ? X1 : X2;
+          Y = first ? Y1 : Y2;
+          Sx = first ? S1 : S2;
+          Z = first ? Z1 : Z2;
+          if constexpr (CV == 2) XI = first ? XI1 : XI2;
+          n += first ? 1 : 2;
+          exited = first ? e1 : e2;
+          if (!exited && n >= kmax) { exited = true; trunc = true; }
+        }
       } else if (alive && !exited) {
-       // two Philox pairs (four steps) between exit checks of the warp
+       // extended-exit kernels (per-knot steps, Gobet-Menozzi exits, the mixed
+       // GM/EM run): two Philox pairs (four steps) between exit checks, one
+       // branch per step (the two-step form above spills more here)
 #pragma unroll 1
        for (int pair = 0; pair < 2; ++pair) {
         if (exited) break;
@@ -934,105 +1192,14 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
     const bool leaving = alive && exited;
     bool gm_rec = false;  // a Gobet-Menozzi exit of a mixed run: recorded, the path goes on
     if constexpr (kMixed) gm_rec = leaving && gm_phase;
-    double bc = 0.0;
-    int side = 0, flags = 0;
-    float Yk = 1.0f, sl = 0.f, s_line = 0.f;
-    int col_a = -1, col_b = -1;
-    float wa = 0.f, wb = 0.f;
-    bool rbf_exit = false;  // EXT + RBF stencils: weights come from the warp loop below
-    if (leaving) {
-      const Stage& H = S.st(st);
-      const KnotDesc& kd = H.kd;
-      unsigned long long* acc = S.acc(st);
-      float ov[4] = {X - bx1, Y - by1, bx0 - X, by0 - Y};
-      if constexpr (EXT && !const_sigma<COEF>()) {
-        // overshoots past each side moved by its own shift (a constant s, or
-        // no shift, gives the lane's moved box, used above)
-        if (gmc > 0.f) {
-          float sh[4];
-          gm_shifts<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk, yk, X, Y, gmc, P.trig_direct,
-                          sh);
-          const float* tb = kd.box;
-          ov[0] = X - (tb[1] - sh[0]);
-          ov[1] = Y - (tb[3] - sh[1]);
-          ov[2] = (tb[0] + sh[2]) - X;
-          ov[3] = (tb[2] + sh[3]) - Y;
-        }
-      }
-      // smallest positive overshoot (ties to the earlier side), else (a path
-      // truncated inside the box) the largest; the running best stays in a
-      // register so the overshoots need no indexed (local-memory) array
-      side = -1;
-      float best = 0.f;
-#pragma unroll
-      for (int o = 0; o < 4; ++o)
-        if (ov[o] > 0.f && (side < 0 || ov[o] < best)) { side = o; best = ov[o]; }
-      if (side < 0) {
-        side = 0;
-        best = ov[0];
-#pragma unroll
-        for (int o = 1; o < 4; ++o)
-          if (ov[o] > best) { side = o; best = ov[o]; }
-      }
-      if constexpr (has_c<COEF>()) Yk = ex2_approx(Sx);
-      bc = (double)Z;
-      if constexpr (CV != 0) bc += (double)XI;
-      const bool vertical = (side == 0 || side == 2);
-      flags = trunc ? 1 : 0;
-      if ((kd.dirbits >> side) & 1) {
-        // exit on the boundary of Omega: Y g at the normal projection
-        float along = vertical ? (yk + Y) : (xk + X);
-        along = vertical ? fminf(fmaxf(along, H.y0), H.y1) : fminf(fmaxf(along, H.x0), H.x1);
-        const float line = vertical ? fmaf((float)kd.line[side], H.dx, H.x0)
-                                    : fmaf((float)kd.line[side], H.dy, H.y0);
-        bc += (double)Yk * (double)g_value<COEF>(H, vertical ? line : along, vertical ? along : line);
-      } else {
-        // exit on an interface: interpolation on the side's extended stencil
-        const int a = kd.a[side], b = kd.b[side];
-        const int kal = vertical ? kd.kj : kd.ki;
-        sl = (float)(kal - a) + (vertical ? Y * H.inv_dy : X * H.inv_dx);
-        const float smax = (float)(b - a);
-        if (sl < 0.f) { sl = 0.f; flags |= 2; }
-        if (sl > smax) { sl = smax; flags |= 2; }
-        s_line = (float)a + sl;
-        if constexpr (EXT) rbf_exit = prob_desc(P, H.prob).rbf_coef != nullptr;
-        if (!rbf_exit) {
-          // linear: the two nearest stencil knots
-          int t = (int)floorf(sl);
-          if (t >= b - a) t = b - a - 1;
-          const float lam = sl - (float)t;
-          // Y (1 - lam) and Y lam in 2^-30 units: q0 + q1 = qY exactly, so the
-          // path deposits its whole weight Y on the two knots (G 1 = b holds
-          // exactly when c = f = 0 and g = 1).
-          const unsigned long long qY = __float2ull_rn(Yk * kFixedOne);
-          const unsigned long long q1 = __float2ull_rn((Yk * lam) * kFixedOne);
-          const unsigned long long qw[2] = {qY - q1, q1};
-          const int lmax = vertical ? H.LY : H.LX;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int tl = a + t + q;
-            if (tl == 0 || tl == lmax) {
-              const int li = vertical ? kd.line[side] : tl;
-              const int lj = vertical ? tl : kd.line[side];
-              bc += (double)qw[q] * kFixedInv *
-                    (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
-                                          fmaf((float)lj, H.dy, H.y0));
-            } else {
-              const int slot = kd.off[side] + t + q;
-              if (!gm_rec) atomicAdd(acc + slot, qw[q]);
-              if constexpr (RECORD) {
-                const ProbDesc& D = prob_desc(P, H.prob);
-                const int c = D.slot2csr[kd.slot_base + slot];
-                const int col = D.col[c];
-                const float wv = (float)((double)qw[q] * kFixedInv);
-                if (q == 0) { col_a = col; wa = wv; }
-                else { col_b = col; wb = wv; }
-              }
-            }
-          }
-        }
-      }
-    }
+    ExitResult E;
+    if (leaving)
+      E = resolve_exit<COEF, RECORD, CV, EXT>(S, P, st, xk, yk, X, Y, Sx, Z, XI, trunc, bx0, bx1,
+                                              by0, by1, gmc, gm_rec);
+    double& bc = E.bc;
+    const int side = E.side, flags = E.flags;
+    const float Yk = E.Yk, sl = E.sl;
+    const bool rbf_exit = E.rbf_exit;  // EXT + RBF stencils: weights come from the warp loop below
     if constexpr (EXT) {
       // RBF stencils (Eq. 21-22): every knot j of the exit side's stencil gets
       // Y H_j(s).  The whole warp serves one exiting lane at a time, a knot per
@@ -1085,15 +1252,7 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         my_trunc += (flags & 1);
         my_clamp += (flags >> 1) & 1;
       }
-      if constexpr (RECORD) {
-        const ProbDesc& D = prob_desc(P, S.st(st).prob);
-        const int64_t idx = (D.path_prefix ? D.path_prefix[kk] : (int64_t)kk * D.n_paths) + p;
-        PathRecordDev R;
-        R.steps = n; R.side_flags = side | (flags << 8); R.col_a = col_a; R.col_b = col_b;
-        R.w_a = wa; R.w_b = wb; R.b_contrib = (float)bc; R.Y = Yk;
-        R.xi = XI; R.s_line = s_line;
-        (gm_rec ? P.records_gm : P.records)[idx] = R;
-      }
+      if constexpr (RECORD) write_record(S, P, st, kk, p, n, E, XI, gm_rec);
       if (!gm_rec) atomicAdd(&S.st(st).bsum, bc);  // one FP64 shared atomic per exit
     }
     if constexpr (kMixed) {

@@ -332,7 +332,10 @@ def test_batch_host_buffers_match_device_calls():
         assert np.array_equal(col[i], P.col.cpu().numpy())
         assert np.allclose(val[i], P.val.cpu().numpy(), rtol=1e-11, atol=1e-14)
         assert np.allclose(b[i], P.b.cpu().numpy(), rtol=1e-11, atol=1e-14)
-        assert np.allclose(u[i], P.u.cpu().numpy(), rtol=1e-8, atol=1e-11)
+        # both solves stop at a relative residual of 1e-12 from b's that differ
+        # in FP64 summation order: u agrees to the solve tolerance times cond(G)
+        ud = P.u.cpu().numpy()
+        assert np.abs(u[i] - ud).max() <= 1e-8 * np.abs(ud).max()
     bad = [x.copy() for x in Nh]
     bad[1][0] = 2 ** 31
     with pytest.raises(pdds.PddsError) as e:
