@@ -507,7 +507,8 @@ def main():
                     help="timed steps (default: 10 for the batched config 3, 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "e1"],
+    ap.add_argument("--config", default="cfg3",
+                    choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "cfg5_network", "e1", "e1_bias"],
                     help="workload (default: config 3, the largest single-GPU configuration)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per knot (small profiling cases; not a bench line)")
@@ -517,6 +518,9 @@ def main():
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
+    ap.add_argument("--fit-data", default="knots+boundary", choices=["knots", "knots+boundary"],
+                    help="what the e1 pipeline's network is fitted to: the warm-up nodal values, "
+                         "plus g on the boundary")
     ap.add_argument("--interp", default="linear", choices=["linear", "rbf"],
                     help="stencil interpolation of the e1 pipeline (Sec. 2.1 RBF or linear)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -536,10 +540,14 @@ def main():
         return run_reference(args)
     if args.config == "cfg5":
         return run_cv_study(args)
+    if args.config == "cfg5_network":
+        return run_cv_network(args)
     if args.config == "cfg3":
         return run_batch(args)
     if args.config == "e1":
         return run_e1(args)
+    if args.config == "e1_bias":
+        return run_e1_bias(args)
     return run_gpu(args)
 
 
@@ -697,6 +705,56 @@ def run_batch(args):
     return 0
 
 
+def run_cv_network(args):
+    """Config 5 with the in-path network control variate (Eq. 37; the
+    network's gradient on the tensor cores in every step): a step is one
+    assembly + solve at N paths per knot (default 1881, the CV study's budget
+    for the plain estimator's error) with the seeded initial network v_theta
+    (the kernel's cost does not depend on the parameter values)."""
+    import torch
+    from paper_2301_05780_gb300 import pdds
+    torch.cuda.set_device(0)
+    w = workload("cfg5")
+    w.n_paths = args.paths or 1881
+    P = pdds.Problem(w)
+    from paper_2301_05780_gb300 import workloads as W
+    theta = torch.tensor(W.mlp_init(), dtype=torch.float32, device="cuda")
+    pdds.pdds_set_control_variate(P.ctx, theta)
+    launch = (pdds.pdds_get_launch(P.ctx) if args.no_autotune
+              else pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed))
+    pdds.pdds_set_timing(P.ctx, True)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.assemble(stream)
+        pdds.pdds_stats(P.ctx)
+    kms, steps, t_ms = [], 0, 0.0
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            P.assemble(stream)
+            P.solve(rtol=1e-10, maxit=5000, stream=stream)
+            b_.record(stream)
+            st = pdds.pdds_stats(P.ctx)
+            torch.cuda.synchronize()
+            t_ms += a.elapsed_time(b_)
+            kms.append(st["path_kernel_ms"])
+            steps += st["path_steps"]
+    line = {"metric": METRIC, "value": steps / (t_ms * 1e-3), "unit": "path-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "cfg5_network_cv", "knots": P.n, "paths_per_knot": w.n_paths,
+                       "dt": w.dt, "path_steps_per_step": steps / args.steps,
+                       "kernel_ms": float(np.mean(kms)),
+                       "launch": {"block": launch[0], "unit_paths": launch[2],
+                                  "exit_batch": launch[3]},
+                       "network": "seeded initial v_theta (2-64-64-1, SiLU)"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_cv_study(args):
     """Config 5: plain estimator vs the learned control variate, time to the
     same interfacial statistical error (one JSON line; not the default bench)."""
@@ -727,6 +785,86 @@ PAPER_E1 = {"phase1": {"max": 0.074, "rmse": 0.016, "frac_below_eps": 0.4898},
             "mean_vrf": 31.37, "mean_bias_at_h0": 3e-5}
 
 
+def _e1_exact_grad(grid: dict, per_interval: int = 2):
+    """grad u of Eq. 43 at the nodes of a grid of `per_interval` nodes per knot
+    spacing over Omega (the look-up-table grid of the e1 pipeline), by central
+    differences of the closed form in FP64 (step 1e-4: error ~1e-10)."""
+    nx = per_interval * grid["Hx"] * grid["m"] + 1
+    ny = per_interval * grid["Hy"] * grid["m"] + 1
+    X, Y = np.meshgrid(np.linspace(grid["x0"], grid["x1"], nx),
+                       np.linspace(grid["y0"], grid["y1"], ny))
+    d = 1e-4
+
+    def u(x, y):
+        return exact_solution(5, np.stack([x.ravel(), y.ravel()], 1)).reshape(x.shape)
+    gx = (u(X + d, Y) - u(X - d, Y)) / (2 * d)
+    gy = (u(X, Y + d) - u(X, Y - d)) / (2 * d)
+    return np.stack([gx, gy], axis=-1).astype(np.float32)
+
+
+def run_e1_bias(args):
+    """The calibration estimates of Sec. 4.1-4.2 on the paper's problem, on
+    every 10th knot with the exact nodal u as patch data (so that only the
+    path discretisation and the sampling enter):
+      * Eq. 36's estimate of E[phi_EM - phi_GM] at h = 0.08, 0.04, 0.02 with
+        N = 1000 (the paper's N0') and N = 64,000 paths per knot: its mean,
+        the mean of |gap| / 2 (Eq. 35, what the pipeline reports) and the
+        sampling noise of the gap, sd(phi_EM - phi_GM) / sqrt(N);
+      * the predicted variance-reduction factor 1 / (1 - rho^2) of Eq. 39 at
+        h = 0.08, N = 1000, with the exact grad u of Eq. 43 as the look-up table
+        (the best any warm-up solution can give)."""
+    import torch
+    from paper_2301_05780_gb300 import pdds
+    torch.cuda.set_device(0)
+    w = workload("e1")
+    P = pdds.Problem(w)
+    n = P.n
+    xy = pdds.pdds_knot_coords(P.ctx)
+    u0 = torch.tensor(exact_solution(w.coef_id, xy), dtype=torch.float64, device=P.dev)
+    rows = np.arange(0, n, 10)
+    mom = torch.empty(n, pdds.CAL_NMOM, dtype=torch.float64, device=P.dev)
+
+    def calibrate(h, N, seed):
+        budgets = np.zeros(n, dtype=np.int64)
+        budgets[rows] = N
+        pdds.pdds_calibrate(P.ctx, u0, mom, 0, torch.from_numpy(budgets).to(P.dev), h, seed)
+        M = mom.cpu().numpy()[rows]
+        cnt = M[:, 0]
+        gap = M[:, 1] / cnt
+        var_d = np.maximum(M[:, 2] - cnt * gap ** 2, 0.0) / (cnt - 1)
+        mphi = M[:, 3] / cnt
+        var_phi = np.maximum(M[:, 4] - cnt * mphi ** 2, 0.0) / (cnt - 1)
+        mxi = M[:, 5] / cnt
+        var_xi = np.maximum(M[:, 6] - cnt * mxi ** 2, 0.0) / (cnt - 1)
+        cov = (M[:, 7] - cnt * mphi * mxi) / (cnt - 1)
+        rho2 = np.where(var_phi * var_xi > 0, cov ** 2 / np.maximum(var_phi * var_xi, 1e-300), 0.0)
+        return gap, np.sqrt(var_d / cnt), rho2
+
+    runs = []
+    with Clocks(0) as clk:
+        for h in (0.08, 0.04, 0.02):
+            for N in (1000, 64000):
+                gap, noise, _ = calibrate(h, N, w.seed + 1)
+                runs.append({"h": h, "N": N, "mean_gap": float(gap.mean()),
+                             "mean_abs_gap_half": float(np.abs(gap).mean() / 2),
+                             "rms_gap": float(np.sqrt(np.mean(gap ** 2))),
+                             "mean_noise_of_gap": float(noise.mean()),
+                             # E|gap| / 2 of a zero-mean Gaussian gap with that noise
+                             "pure_noise_abs_gap_half": float(noise.mean() * math.sqrt(2 / math.pi) / 2)})
+        pdds.pdds_set_control_variate_grid(P.ctx, torch.from_numpy(_e1_exact_grad(w.grid)).cuda())
+        _, _, rho2 = calibrate(0.08, 1000, w.seed + 1)
+        pdds.pdds_set_control_variate_grid(P.ctx, None)
+    line = {"metric": "calibration estimates (Eq. 35-36, 39) on the paper's problem",
+            "config": {"workload": w.name, "rows": int(len(rows)), "patch_data": "exact u"},
+            "bias_runs": runs,
+            "vrf_exact_gradient_table": {"h": 0.08, "N": 1000,
+                                         "mean_predicted_vrf": float(np.mean(1 / np.maximum(1 - rho2, 1e-12))),
+                                         "median_predicted_vrf": float(np.median(1 / np.maximum(1 - rho2, 1e-12)))},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_e1(args):
     """The paper's experiment (Sec. 5.1) through the calibrated three-phase
     pipeline (warm-up, mixed GM/EM calibration with Eq. 40-41, production
@@ -739,7 +877,8 @@ def run_e1(args):
     w = workload("e1")
     x = w.extra
     kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
-              rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps)
+              rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps,
+              boundary_samples=args.fit_data == "knots+boundary")
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []
@@ -763,6 +902,7 @@ def run_e1(args):
                        "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
                        "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
                        "control_variate": args.cv, "train_steps": args.train_steps,
+                       "fit_data": args.fit_data,
                        "note": "path-steps simulated in the three phases (the calibration's "
                                "mixed GM/EM paths once, to their naive exits)"},
             "pipeline": {

@@ -361,6 +361,17 @@ pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target, i
 pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, float* v,
                           float* grad_xy, void* cuda_stream);
 
+/* Samples of the boundary data g of Eq. 6 on the boundary of Omega, for the
+ * fit of v_theta (the warm-up nodal values say nothing about u between the
+ * outermost knots and the boundary, where g is known exactly): n_per_side
+ * points on each side, E (x = x1), N (y = y1), W (x = x0), S (y = y0) in that
+ * order, at the midpoints of n_per_side equal intervals (corners excluded),
+ * with g evaluated on the device as the path kernel evaluates it at a
+ * boundary exit.  xy: DEVICE float [4 n_per_side][2]; g: DEVICE float
+ * [4 n_per_side].  Asynchronous.  EINVAL for n_per_side outside [1, 2^26]. */
+pdds_status pdds_boundary_samples(const pdds_ctx* ctx, int32_t n_per_side, float* xy, float* g,
+                                  void* cuda_stream);
+
 /* Attach v_theta (DEVICE theta, copied and staged) to the context: from then
  * on pdds_assemble adds xi_K = -sum_n Y_n s(X_n) grad v(X_n) . dW_n to every
  * path's b contribution (Eq. 37, left-point Ito sum), which leaves E[b]

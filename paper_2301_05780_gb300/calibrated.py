@@ -3,9 +3,9 @@ the pseudocode of Sec. 4.3):
 
   Phase I    warm-up: G0, b0 with N0 paths and step h0 at every knot (Gobet-
              Menozzi exits), solve -> nodal u0
-  fit        v_theta ~ u0 at the knots: the control variate F = sigma^T grad v
-             of Eq. 37, with a small network in place of the paper's patch-wise
-             lookup table of grad u0
+  fit        v_theta ~ u0 at the knots and g on the boundary: the control
+             variate F = sigma^T grad v of Eq. 37, with a small network in place
+             of the paper's patch-wise lookup table of grad u0
   Phase II   calibration: N0' mixed GM/EM paths per knot at step h0' with u0
              as patch data and xi drawn alongside -> per-knot moments; Eq. 40-41
              -> per-knot steps h_i and budgets N_i (multiples of N_job)
@@ -36,8 +36,9 @@ def _sync_ms(fn):
     return out, 1e3 * (time.perf_counter() - t0)
 
 
-def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
-    """Fits v_theta to the nodal values u0 at the knots xy with the library's
+def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev, boundary=None):
+    """Fits v_theta to the nodal values u0 at the knots xy (and, given
+    boundary = (xy_b, g_b), to the boundary data there) with the library's
     Adam kernels, on inputs scaled to [-1, 1]^2 and targets standardised, and
     folds both affine maps into the first and last layers, so that the
     returned theta (device float32) evaluates v in the problem's coordinates:
@@ -46,6 +47,9 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
     c = np.array([(grid["x0"] + grid["x1"]) / 2, (grid["y0"] + grid["y1"]) / 2])
     s = np.array([(grid["x1"] - grid["x0"]) / 2, (grid["y1"] - grid["y0"]) / 2])
     u = u0.detach().double().cpu().numpy()
+    if boundary is not None:
+        xy = np.concatenate([xy, boundary[0].detach().double().cpu().numpy()])
+        u = np.concatenate([u, boundary[1].detach().double().cpu().numpy()])
     mean, sd = float(u.mean()), float(u.std()) or 1.0
     xy_n = torch.tensor((xy - c) / s, dtype=torch.float32, device=dev)
     t_n = torch.tensor((u - mean) / sd, dtype=torch.float32, device=dev)
@@ -66,13 +70,15 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev):
 def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | None = None,
         h0p: float | None = None, control_variate: bool = True, train_steps: int = 1500,
         lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
-        rbf_shape: float = 0.0, cv_kind: str = "table") -> dict:
+        rbf_shape: float = 0.0, cv_kind: str = "table", boundary_samples: bool = True) -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
     and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
     instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
     cv_kind: "table" tabulates grad v_theta on a grid of half the knot spacing
     (the paper's look-up table of Sec. 4.2, one cell read per step) or "network"
     evaluates v_theta in the path (two 64 x 64 products per step).
+    boundary_samples: the fit also sees g at the boundary points of the
+    lattice (pdds_boundary_samples), where u is known exactly.
     Returns the nodal solutions of Phases I and III, the calibration (h_i,
     N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and
     path-step counts."""
@@ -106,14 +112,19 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     theta = None
     if control_variate:
         xy = pdds.pdds_knot_coords(P.ctx)
-        (theta, hist), tfit = _sync_ms(lambda: fit_network(xy, u0, w.grid, train_steps, lr, dev))
+
+        def fit():
+            bnd = (pdds.pdds_boundary_samples(P.ctx, w.grid["Hx"] * w.grid["m"], dev)
+                   if boundary_samples else None)
+            return fit_network(xy, u0, w.grid, train_steps, lr, dev, boundary=bnd)
+        (theta, hist), tfit = _sync_ms(fit)
         if cv_kind == "network":
             pdds.pdds_set_control_variate(P.ctx, theta)
             ttab = 0.0
         else:
             _, ttab = _sync_ms(lambda: tabulate_gradient(P.ctx, theta, w.grid, dev))
         out["fit"] = {"ms": tfit + ttab, "steps": train_steps, "final_loss": float(hist[-1]),
-                      "cv_kind": cv_kind}
+                      "cv_kind": cv_kind, "boundary_samples": boundary_samples}
 
     # Phase II: mixed GM/EM calibration and Eq. 40-41
     mom = torch.empty(n, pdds.CAL_NMOM, dtype=torch.float64, device=dev)

@@ -764,6 +764,19 @@ pdds_status pdds_get_launch(const pdds_ctx* c, int32_t* block, int32_t* per_sm,
   return PDDS_OK;
 }
 
+pdds_status pdds_boundary_samples(const pdds_ctx* c, int32_t n_per_side, float* xy, float* g,
+                                  void* stream) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "boundary_samples: NULL context");
+  if (n_per_side < 1 || n_per_side > (1 << 26) || !xy || !g)
+    return fail(const_cast<pdds_ctx*>(c), PDDS_EINVAL,
+                "boundary_samples: need 1 <= n_per_side <= 2^26 and device xy, g");
+  (void)cudaGetLastError();
+  const double dom[4] = {c->grid.x0, c->grid.x1, c->grid.y0, c->grid.y1};
+  CK(const_cast<pdds_ctx*>(c), pdds::launch_boundary_samples(c->coef_id, dom, c->params, n_per_side,
+                                                               xy, g, (cudaStream_t)stream));
+  return PDDS_OK;
+}
+
 pdds_status pdds_set_philox_tag(pdds_ctx* c, uint32_t tag) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_philox_tag: NULL context");
   c->tag = tag;

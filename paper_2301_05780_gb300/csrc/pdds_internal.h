@@ -172,6 +172,10 @@ cudaError_t launch_plan(const double* moments, int64_t n, double eps, double h0,
                         int64_t n_job, double* h_out, int64_t* n_out, double* diag,
                         cudaStream_t stream);
 
+// Boundary data g at 4 n points of the boundary of Omega (pdds_path.cu).
+cudaError_t launch_boundary_samples(int coef, const double dom[4], const double params[8], int n,
+                                    float* xy, float* g, cudaStream_t stream);
+
 // FP64 BiCGSTAB building blocks (pdds_solve.cu).
 struct SolveScalars;
 cudaError_t bicgstab_device(const int32_t* row_ptr, const int32_t* col, const double* val,

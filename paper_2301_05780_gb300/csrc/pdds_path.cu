@@ -164,6 +164,54 @@ cudaError_t launch_cv_cells(const float* nodes, int nx, int ny, float* cells, cu
   return cudaGetLastError();
 }
 
+// Samples of the boundary data g (Eq. 6) at the midpoints of n equal
+// intervals of each side of Omega (E, N, W, S), evaluated as the path kernel
+// evaluates g at an exit on the boundary.
+struct Params8 {
+  float v[8];
+};
+template <int COEF>
+__global__ void boundary_samples_kernel(float x0, float x1, float y0, float y1, int n, Params8 prm,
+                                        float* __restrict__ xy, float* __restrict__ g) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 4 * (int64_t)n) return;
+  const int side = (int)(i / n);
+  const float t = ((float)(i % n) + 0.5f) / (float)n;
+  const float ax = fmaf(t, x1 - x0, x0), ay = fmaf(t, y1 - y0, y0);
+  const float x = side == 0 ? x1 : side == 2 ? x0 : ax;
+  const float y = side == 1 ? y1 : side == 3 ? y0 : ay;
+  Stage H;  // g reads only the set's constants
+  for (int q = 0; q < 8; ++q) H.params[q] = prm.v[q];
+  xy[2 * i] = x;
+  xy[2 * i + 1] = y;
+  g[i] = g_value<COEF>(H, x, y);
+}
+
+cudaError_t launch_boundary_samples(int coef, const double dom[4], const double params[8], int n,
+                                    float* xy, float* g, cudaStream_t s) {
+  Params8 prm;
+  for (int q = 0; q < 8; ++q) prm.v[q] = (float)params[q];
+  const float x0 = (float)dom[0], x1 = (float)dom[1], y0 = (float)dom[2], y1 = (float)dom[3];
+  const unsigned blocks = (unsigned)((4 * (int64_t)n + 255) / 256);
+  switch (coef) {
+    case PDDS_COEF_LAPLACE_EXPSIN:
+      boundary_samples_kernel<0><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    case PDDS_COEF_MANUFACTURED:
+      boundary_samples_kernel<1><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    case PDDS_COEF_VARSIGMA:
+      boundary_samples_kernel<2><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    case PDDS_COEF_TABLE:
+      boundary_samples_kernel<3><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    case PDDS_COEF_CONSTANT:
+      boundary_samples_kernel<4><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    case PDDS_COEF_POISSON_E1:
+      boundary_samples_kernel<5><<<blocks, 256, 0, s>>>(x0, x1, y0, y1, n, prm, xy, g); break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 size_t stage_header_bytes() { return (size_t)kStageHdr; }
 
 cudaError_t launch_finalize(const int32_t* row_ptr, const int32_t* col, double* val, double* b,

@@ -3,7 +3,8 @@ production scheme (Sec. 4.1-4.2, pseudocode Phase I and III) with the lookup
 table of grad u0 replaced by a network v_theta fitted to the warm-up solution.
 
   Phase I   assemble G, b with N0 paths per knot, solve -> u0 at the knots
-  fit       v_theta ~ u0 on the knots with the library's FP32 Adam kernels
+  fit       v_theta ~ u0 on the knots and g on the boundary with the library's
+            FP32 Adam kernels
   Phase III attach v_theta (xi = -int Y sigma grad v_theta . dW, Eq. 37) and
             assemble with N paths per knot, solve -> u
 
@@ -41,8 +42,9 @@ def _ms(fn):
 def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float = 3e-3,
                         seed_offset: int = 7919, max_points: int = 16384) -> CVResult:
     """Phase I on P's grid with n0 paths per knot, then fit v_theta to u0 at
-    (at most max_points, seeded) knots: u0 is smooth at the network's scale,
-    so a subset trains it as well as every knot for a fraction of the cost."""
+    (at most max_points, seeded) knots and to g at the lattice's boundary
+    points: u0 is smooth at the network's scale, so a subset of the knots
+    trains it as well as every knot for a fraction of the cost."""
     import torch
     w = P.w
     dev = P.dev
@@ -58,6 +60,10 @@ def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float =
         g = torch.Generator(device="cpu").manual_seed(int(w.seed) & 0x7fffffff)
         pick = torch.randperm(P.n, generator=g)[:max_points].to(dev)
         xy, u0 = xy[pick].contiguous(), u0[pick].contiguous()
+    # plus the boundary data g at the lattice's boundary points (u is known there)
+    bxy, bg = pdds.pdds_boundary_samples(P.ctx, w.grid["Hx"] * w.grid["m"], dev)
+    xy = torch.cat([xy, bxy]).contiguous()
+    u0 = torch.cat([u0, bg]).contiguous()
     theta = torch.tensor(W.mlp_init(), dtype=torch.float32, device=dev)
     hist = [None]
 

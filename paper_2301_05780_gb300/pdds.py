@@ -95,6 +95,7 @@ _SIGS = {
     "pdds_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "pdds_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
     "pdds_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "pdds_boundary_samples": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "pdds_set_control_variate": (C.c_int, [_P, _P]),
     "pdds_set_control_variate_grid": (C.c_int, [_P, _P, C.c_int32, C.c_int32]),
     "pdds_assemble_solve_host": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_double,
@@ -368,6 +369,18 @@ def pdds_mlp_eval(theta, xy, stream=None):
     g = torch.empty(n, 2, dtype=torch.float32, device=xy.device)
     _check(lib().pdds_mlp_eval(_dptr(theta), _dptr(xy), n, _dptr(v), _dptr(g), _stream(stream)))
     return v, g
+
+
+def pdds_boundary_samples(ctx, n_per_side, device=None, stream=None):
+    """(xy [4n, 2], g [4n]) float32 device tensors: g at n points per side of
+    the boundary of Omega (E, N, W, S)."""
+    import torch
+    dev = device if device is not None else torch.device("cuda")
+    xy = torch.empty(4 * n_per_side, 2, dtype=torch.float32, device=dev)
+    g = torch.empty(4 * n_per_side, dtype=torch.float32, device=dev)
+    _check(lib().pdds_boundary_samples(ctx, int(n_per_side), _dptr(xy), _dptr(g), _stream(stream)),
+           ctx)
+    return xy, g
 
 
 def pdds_set_control_variate(ctx, theta):

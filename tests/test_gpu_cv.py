@@ -190,3 +190,21 @@ def test_cv_reduces_variance_and_keeps_the_mean(trained_theta):
     P.assemble()
     torch.cuda.synchronize()
     assert np.allclose(P.b.cpu().numpy(), b0, rtol=1e-11, atol=1e-14)
+
+
+def test_boundary_samples_are_the_boundary_data():
+    """pdds_boundary_samples: midpoints of equal intervals on the four sides
+    (E, N, W, S) and g there, against the closed-form u of config 2 (g = u on
+    the boundary), within FP32 evaluation error."""
+    w = W.config2()
+    P = pdds.Problem(w)
+    n = 37
+    xy, g = pdds.pdds_boundary_samples(P.ctx, n)
+    xy, g = xy.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    t = (np.arange(n) + 0.5) / n
+    want = np.concatenate([np.stack([np.ones(n), t], 1), np.stack([t, np.ones(n)], 1),
+                           np.stack([np.zeros(n), t], 1), np.stack([t, np.zeros(n)], 1)])
+    assert np.abs(xy - want).max() < 1e-6
+    assert np.abs(g - u_exact(want[:, 0], want[:, 1])).max() < 2e-5
+    with pytest.raises(pdds.PddsError):
+        pdds.pdds_boundary_samples(P.ctx, 0)
