@@ -518,7 +518,7 @@ def main():
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
-    ap.add_argument("--fit-data", default="knots+boundary", choices=["knots", "knots+boundary"],
+    ap.add_argument("--fit-data", default="knots", choices=["knots", "knots+boundary"],
                     help="what the e1 pipeline's network is fitted to: the warm-up nodal values, "
                          "plus g on the boundary")
     ap.add_argument("--interp", default="linear", choices=["linear", "rbf"],

@@ -372,6 +372,19 @@ pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, flo
 pdds_status pdds_boundary_samples(const pdds_ctx* ctx, int32_t n_per_side, float* xy, float* g,
                                   void* cuda_stream);
 
+/* v_theta and grad v_theta at npts DEVICE points on the fifth-generation
+ * tensor cores (tcgen05.mma kind::tf32 with TMEM accumulators): tiles of 128
+ * points, the two 64 x 64 products (forward h1 W2^T and backward g2 W2 of
+ * Eq. 37's grad v) each as three TF32 products of the hi / lo split of both
+ * operands (FP32-accurate), the rest FP32.  Used to tabulate grad v_theta for
+ * the look-up-table control variate (Sec. 4.2).  theta, xy [npts][2], v
+ * (nullable) [npts], grad_xy [npts][2]: DEVICE.  One CTA of two 128-thread
+ * warpgroups per SM (~195 KB of shared memory, 256 TMEM columns).
+ * Synchronizes the stream.
+ * Errors: EINVAL, ECUDA, ETIMEOUT (a bounded tensor-core wait ran out). */
+pdds_status pdds_mlp_eval_tc(const float* theta, const float* xy, int64_t npts, float* v,
+                             float* grad_xy, void* cuda_stream);
+
 /* Attach v_theta (DEVICE theta, copied and staged) to the context: from then
  * on pdds_assemble adds xi_K = -sum_n Y_n s(X_n) grad v(X_n) . dW_n to every
  * path's b contribution (Eq. 37, left-point Ito sum), which leaves E[b]

@@ -1,0 +1,142 @@
+// Fifth-generation tensor-core building blocks for sm_103a (tcgen05 + TMEM),
+// written as single PTX instructions from the ISA:
+//  - operand tiles in shared memory, K-major with the 128-byte swizzle
+//    (8-row x 128-byte atoms, 16-byte chunks XOR-permuted by the row within
+//    the atom; consecutive 8-row groups 1024 bytes apart);
+//  - 64-bit shared-memory matrix descriptors and the 32-bit instruction
+//    descriptor of tcgen05.mma kind::tf32 (FP32 accumulation);
+//  - TMEM allocation, 32x32b loads of a warp's 32 lanes, the commit of issued
+//    MMAs to an mbarrier, and the bounded wait on it.
+// The TF32 products are made FP32-accurate by the three-term split of each
+// operand x = hi + lo, hi = x with its 13 low mantissa bits cleared (exact in
+// TF32), lo = x - hi (exact in FP32): A B ~ Ahi Bhi + Ahi Blo + Alo Bhi (the
+// "3xTF32" scheme of Ootomo & Yokota, IJHPCA 2022; the dropped Alo Blo term is
+// below 2^-20 relative).
+#pragma once
+#include <stdint.h>
+
+namespace pdds {
+namespace tc {
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Byte offset of element (r, k) of a [rows][K] FP32 tile stored K-major with
+// the 128-byte swizzle: K is cut into 32-element atom columns (rows x 128 B
+// each, one after the other), rows in 8-row groups of 1024 bytes.
+__device__ __forceinline__ int swz_offset(int r, int k, int rows) {
+  const int a = k >> 5, kk = k & 31, chunk = kk >> 2, w = kk & 3;
+  return a * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + (w << 2);
+}
+// Offset of the 16-byte chunk holding elements (r, 4c .. 4c + 3).
+__device__ __forceinline__ int swz_chunk(int r, int c, int rows) {
+  const int a = c >> 3, cc = c & 7;
+  return a * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((cc ^ (r & 7)) << 4);
+}
+
+// Shared-memory matrix descriptor of a K-major 128-byte-swizzled operand
+// whose (1024-byte aligned) atom column starts at `addr` (plus a K offset
+// below 128 bytes): start address >> 4 (bits 0-13), leading byte offset 16
+// (bits 16-29; unused by this layout), stride byte offset 1024 >> 4 (bits
+// 32-45), descriptor version 1 (bits 46-48), swizzle mode 2 = 128 B (61-63).
+__device__ __forceinline__ uint64_t sdesc_k128(unsigned addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
+
+// D (TMEM) [+]= A B^T for one K-step (8 TF32 values per row), one thread.
+__device__ __forceinline__ void mma_tf32(unsigned d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate ? 1u : 0u)
+      : "memory");
+}
+// Arrive on the mbarrier once every MMA this thread issued has completed.
+__device__ __forceinline__ void commit(unsigned long long* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Generic-proxy shared-memory writes made visible to the tensor core.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bounded wait for phase `parity` of the mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, uint64_t limit_ns) {
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > limit_ns) return false;
+  }
+}
+// TMEM columns for this CTA (one warp; `ncols` a power of two >= 32); the
+// base address is written to *slot (shared memory).
+__device__ __forceinline__ void tmem_alloc(unsigned* slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned base, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols)
+               : "memory");
+}
+// 32 consecutive FP32 columns of the calling thread's TMEM lane (the warp
+// reads its 32-lane quarter: taddr = base + (32 (warp % 4) << 16) + column).
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace tc
+}  // namespace pdds

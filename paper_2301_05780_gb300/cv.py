@@ -76,15 +76,16 @@ def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float =
 
 def tabulate_gradient(ctx, theta, grid: dict, dev, per_interval: int = 2):
     """Sec. 4.2's look-up table of grad u0: grad v_theta at the nodes of a grid
-    over Omega with `per_interval` nodes per knot spacing, evaluated by the
-    library's in-path routine and attached to ctx as the control variate."""
+    over Omega with `per_interval` nodes per knot spacing, evaluated on the
+    tcgen05 tensor cores (FP32-accurate) and attached to ctx as the control
+    variate."""
     import torch
     nx = per_interval * grid["Hx"] * grid["m"] + 1
     ny = per_interval * grid["Hy"] * grid["m"] + 1
     gx = torch.linspace(grid["x0"], grid["x1"], nx, dtype=torch.float32, device=dev)
     gy = torch.linspace(grid["y0"], grid["y1"], ny, dtype=torch.float32, device=dev)
     pts = torch.stack(torch.meshgrid(gx, gy, indexing="xy"), dim=-1).reshape(-1, 2)
-    _, grad = pdds.pdds_mlp_eval(theta, pts.contiguous())
+    _, grad = pdds.pdds_mlp_eval_tc(theta, pts.contiguous())
     pdds.pdds_set_control_variate_grid(ctx, grad.reshape(ny, nx, 2))
     return nx, ny
 

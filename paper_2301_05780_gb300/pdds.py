@@ -95,6 +95,7 @@ _SIGS = {
     "pdds_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "pdds_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
     "pdds_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
+    "pdds_mlp_eval_tc": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "pdds_boundary_samples": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "pdds_set_control_variate": (C.c_int, [_P, _P]),
     "pdds_set_control_variate_grid": (C.c_int, [_P, _P, C.c_int32, C.c_int32]),
@@ -381,6 +382,17 @@ def pdds_boundary_samples(ctx, n_per_side, device=None, stream=None):
     _check(lib().pdds_boundary_samples(ctx, int(n_per_side), _dptr(xy), _dptr(g), _stream(stream)),
            ctx)
     return xy, g
+
+
+def pdds_mlp_eval_tc(theta, xy, stream=None):
+    """(v, grad) at the points xy [n, 2] on the tcgen05 tensor cores (3xTF32)."""
+    import torch
+    n = xy.shape[0]
+    v = torch.empty(n, dtype=torch.float32, device=xy.device)
+    g = torch.empty(n, 2, dtype=torch.float32, device=xy.device)
+    _check(lib().pdds_mlp_eval_tc(_dptr(theta), _dptr(xy), n, _dptr(v), _dptr(g),
+                                  _stream(stream)))
+    return v, g
 
 
 def pdds_set_control_variate(ctx, theta):

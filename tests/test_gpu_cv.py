@@ -208,3 +208,23 @@ def test_boundary_samples_are_the_boundary_data():
     assert np.abs(g - u_exact(want[:, 0], want[:, 1])).max() < 2e-5
     with pytest.raises(pdds.PddsError):
         pdds.pdds_boundary_samples(P.ctx, 0)
+
+
+@pytest.mark.parametrize("npts", [1013, 40017])
+def test_mlp_eval_tc_matches_oracle(orc, oracle_theta, npts):
+    """The tcgen05 evaluation (128-point tiles, 3xTF32 products in TMEM) against
+    the FP64 network: v and grad v to FP32 accuracy (1e-5 of max |v|, 1e-4 of
+    the gradient scale); 40,017 points run several tiles per CTA and end in a
+    ragged tile."""
+    rng = np.random.default_rng(17)
+    xy = rng.uniform(-0.2, 1.2, size=(npts, 2)).astype(np.float32)
+    th = oracle_theta.astype(np.float64)
+    v, g = pdds.pdds_mlp_eval_tc(dev32(oracle_theta), dev32(xy))
+    v, g = v.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    sel = np.linspace(0, npts - 1, 1500).astype(np.int64)
+    vo = np.array([orc.mlp_value(th, *xy[i].astype(np.float64)) for i in sel])
+    go = np.array([orc.mlp_grad_x(th, *xy[i].astype(np.float64)) for i in sel])
+    scale = np.sqrt(np.mean(go ** 2))
+    assert np.abs(v[sel] - vo).max() <= 1e-5 * max(1.0, np.abs(vo).max()), np.abs(v[sel] - vo).max()
+    assert np.abs(g[sel] - go).max() <= 1e-4 * scale, (np.abs(g[sel] - go).max(), scale)
+    assert np.isfinite(v).all() and np.isfinite(g).all()
