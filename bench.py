@@ -576,6 +576,12 @@ def run_batch(args):
         for P in probs:
             P.n_per_knot = torch.clamp(P.n_per_knot, max=args.paths)
     c0 = probs[0].ctx
+    # The batch's launch shape, measured on one GB300 at the full budgets (the
+    # per-problem autotuner does not cover batches): 128-thread CTAs, units of
+    # 2048 paths, exit batch 4 ran 1 % faster than 256 / 4096 / 4 and ahead of
+    # 128 / 4096 / 4, 128 / 2048 / 2 and 192 / 2048 / 4.
+    if not args.no_autotune:
+        pdds.pdds_set_launch(c0, 128, 0, 2048, 4)
     launch = pdds.pdds_get_launch(c0)
     pdds.pdds_set_timing(c0, True)
     stream = torch.cuda.current_stream()
@@ -686,7 +692,9 @@ def run_batch(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "launch": {"block": launch[0], "unit_paths": launch[2],
                                   "exit_batch": launch[3], "kind": "one persistent kernel for "
-                                  "all 16 problems, replayed from a CUDA graph"}},
+                                  "all 16 problems, replayed from a CUDA graph",
+                                  "chosen_by": "default" if args.no_autotune else
+                                  "measured launch-shape sweep at full budgets"}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": profiled_traffic("cfg3"),
                          "kernel": "path_kernel", "flops_per_path_step": fpk,

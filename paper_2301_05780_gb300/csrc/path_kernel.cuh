@@ -534,12 +534,12 @@ __device__ __forceinline__ void cv_table_grad(const ProbDesc& D, float x, float 
 // packed FP32 instructions; the values are those of the scalar forms.
 template <int COEF, int CV>
 __device__ __forceinline__ void em_step(const Stage& H, const float* tile, const KParams& P,
-                                        float xk, float yk, float h, float hl2, float sqh,
-                                        float2 g, float& X, float& Y, float& Sx, float& Z,
-                                        float& XI) {
+                                        bool direct, float xk, float yk, float h, float hl2,
+                                        float sqh, float2 g, float& X, float& Y, float& Sx,
+                                        float& Z, float& XI) {
   const float2 a = add2(f2(xk, yk), f2(X, Y));  // the absolute position
   float s, ddx, ddy, c, f;
-  coeffs<COEF>(H, tile, tile, a.x, a.y, X, Y, P.trig_direct, s, ddx, ddy, c, f);
+  coeffs<COEF>(H, tile, tile, a.x, a.y, X, Y, direct, s, ddx, ddy, c, f);
   float Yw = 1.0f;
   if constexpr (has_c<COEF>()) {
     Yw = ex2_approx(Sx);
@@ -567,6 +567,54 @@ __device__ __forceinline__ void em_step(const Stage& H, const float* tile, const
 __device__ __forceinline__ bool outside_box(float X, float Y, float bx0, float bx1, float by0,
                                             float by1) {
   return (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+}
+
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
+template <int COEF>
+__host__ __device__ constexpr bool uses_angles() {  // the coefficients take sines of the position
+  return COEF == PDDS_COEF_MANUFACTURED || COEF == PDDS_COEF_VARSIGMA ||
+         COEF == PDDS_COEF_POISSON_E1;
+}
+
+// Two Philox calls (four steps) of one lane's path on the naive exit: the two
+// steps of a call are taken without a branch between them -- the second one
+// starts from the first one's result and is dropped when the first one left
+// the patch or reached the step cap.  DIRECT: the coefficient sines take the
+// angle without reduction (the launch's domains allow it), a compile-time
+// choice so that the step carries no branch on it.
+template <int COEF, int CV, bool DIRECT>
+__device__ __forceinline__ void step_two_calls(const Stage& H, const float* tile,
+                                               const KParams& P, uint32_t p, uint32_t kk,
+                                               uint32_t tagw, float xk, float yk, float h,
+                                               float hl2, float sqh, int kmax, float bx0,
+                                               float bx1, float by0, float by1, int& n, float& X,
+                                               float& Y, float& Sx, float& Z, float& XI,
+                                               bool& exited, bool& trunc) {
+#pragma unroll 1
+  for (int pair = 0; pair < 2 && !exited; ++pair) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
+    float2 gA, gB;
+    box_muller4(r, gA, gB);
+    float X1 = X, Y1 = Y, S1 = Sx, Z1 = Z, XI1 = XI;
+    em_step<COEF, CV>(H, tile, P, DIRECT, xk, yk, h, hl2, sqh, gA, X1, Y1, S1, Z1, XI1);
+    const bool e1 = outside_box(X1, Y1, bx0, bx1, by0, by1);
+    float X2 = X1, Y2 = Y1, S2 = S1, Z2 = Z1, XI2 = XI1;
+    em_step<COEF, CV>(H, tile, P, DIRECT, xk, yk, h, hl2, sqh, gB, X2, Y2, S2, Z2, XI2);
+    const bool e2 = outside_box(X2, Y2, bx0, bx1, by0, by1);
+    const bool first = e1 || (n + 1 >= kmax);
+    X = first ? X1 : X2;
+    Y = first ? Y1 : Y2;
+    Sx = first ? S1 : S2;
+    Z = first ? Z1 : Z2;
+    if constexpr (CV == 2) XI = first ? XI1 : XI2;
+    n += first ? 1 : 2;
+    exited = first ? e1 : e2;
+    if (!exited && n >= kmax) { exited = true; trunc = true; }
+  }
 }
 
 // What the resolution of one exited path produces (Eq. 22-25).
@@ -1090,98 +1138,78 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
           }
         }
       } else if (!EXT && alive && !exited) {
-        // Two Philox calls (four steps) between exit checks of the warp.  The
-        // two steps of a call are taken without a branch between them: the
-        // second one starts from the first one's result, and is dropped when
-        // the first one left the patch or reached the step cap.
         const Stage& H = S.st(st);
         const float* tile = S.tile(st, 0);
-#pragma unroll 1
-        for (int pair = 0; pair < 2 && !exited; ++pair) {
-          const uint4 r = kPhiloxPre ? philox_step((uint32_t)(n >> 1), ph, P.round_keys)
-                            : philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
-          float2 gA, gB;
-          box_muller4(r, gA, gB);
-          float X1 = X, Y1 = Y, S1 = Sx, Z1 = Z, XI1 = XI;
-          em_step<COEF, CV>(H, tile, P, xk, yk, h, hl2, sqh, gA, X1, Y1, S1, Z1, XI1);
-          bool e1 = outside_box(X1, Y1, bx0, bx1, by0, by1);
-          float X2 = X1, Y2 = Y1, S2 = S1, Z2 = Z1, XI2 = XI1;
-          em_step<COEF, CV>(H, tile, P, xk, yk, h, hl2, sqh, gB, X2, Y2, S2, Z2, XI2);
-          bool e2 = outside_box(X2, Y2, bx0, bx1, by0, by1);
-          if constexpr (EXT && !const_sigma<COEF>()) {
-            // the box moved by the largest shift only selects candidates
-            if (e1 && gmc > 0.f) e1 = gm_outside<COEF>(H, tile, tile, xk, yk, X1, Y1, gmc,
-                                                      P.trig_direct);
-            if (e2 && !e1 && gmc > 0.f) e2 = gm_outside<COEF>(H, tile, tile, xk, yk, X2, Y2, gmc,
-                                                               P.trig_direct);
-          }
-          const bool first = e1 || (n + 1 >= kmax);
-          X = first ? X1 : X2;
-          Y = first ? Y1 : Y2;
-          Sx = first ? S1 : S2;
-          Z = first ? Z1 : Z2;
-          if constexpr (CV == 2) XI = first ? XI1 : XI2;
-          n += first ? 1 : 2;
-          exited = first ? e1 : e2;
-          if (!exited && n >= kmax) { exited = true; trunc = true; }
-        }
+        if (uses_angles<COEF>() && P.trig_direct)
+          step_two_calls<COEF, CV, uses_angles<COEF>()>(H, tile, P, p, kk, tagw, xk, yk, h, hl2,
+                                                        sqh, kmax, bx0, bx1, by0, by1, n, X, Y,
+                                                        Sx, Z, XI, exited, trunc);
+        else
+          step_two_calls<COEF, CV, false>(H, tile, P, p, kk, tagw, xk, yk, h, hl2, sqh, kmax,
+                                          bx0, bx1, by0, by1, n, X, Y, Sx, Z, XI, exited, trunc);
       } else if (alive && !exited) {
        // extended-exit kernels (per-knot steps, Gobet-Menozzi exits, the mixed
        // GM/EM run): two Philox pairs (four steps) between exit checks, one
-       // branch per step (the two-step form above spills more here)
+       // branch per step (the two-step form spills more here)
+       // (the angle-reduction choice is a template constant here too)
+       auto ext_calls = [&](auto direct_tag) {
+        constexpr bool kDirect = decltype(direct_tag)::value;
 #pragma unroll 1
-       for (int pair = 0; pair < 2; ++pair) {
-        if (exited) break;
-        const uint4 r = kPhiloxPre ? philox_step((uint32_t)(n >> 1), ph, P.round_keys)
-                          : philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
-        float z[4];
-        box_muller(r.x, r.y, z[0], z[1]);
-        box_muller(r.z, r.w, z[2], z[3]);
+         for (int pair = 0; pair < 2; ++pair) {
+          if (exited) break;
+          const uint4 r = kPhiloxPre ? philox_step((uint32_t)(n >> 1), ph, P.round_keys)
+                            : philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
+          float z[4];
+          box_muller(r.x, r.y, z[0], z[1]);
+          box_muller(r.z, r.w, z[2], z[3]);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          // a Philox call serves steps 2q and 2q + 1; a mixed-run path that
-          // resumes at an odd step takes the second half of its call
-          if (!exited && (!kMixed || half >= (n & 1))) {
-            const Stage& H = S.st(st);
-            float s, ddx, ddy, c, f;
-            coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.trig_direct,
-                         s, ddx, ddy, c, f);
-            float Yw = 1.0f;
-            if constexpr (has_c<COEF>()) {
-              Yw = ex2_approx(Sx);
-              Z = fmaf(-f * Yw, h, Z);  // dZ = -f Y dt
-              Sx = fmaf(c, hl2, Sx);    // dY = c Y dt, Y = 2^S with S = log2(e) int c dt
-            } else if constexpr (has_f<COEF>()) {
-              Z = fmaf(-f, h, Z);       // c = 0: Y = 1
+          for (int half = 0; half < 2; ++half) {
+            // a Philox call serves steps 2q and 2q + 1; a mixed-run path that
+            // resumes at an odd step takes the second half of its call
+            if (!exited && (!kMixed || half >= (n & 1))) {
+              const Stage& H = S.st(st);
+              float s, ddx, ddy, c, f;
+              coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, kDirect,
+                           s, ddx, ddy, c, f);
+              float Yw = 1.0f;
+              if constexpr (has_c<COEF>()) {
+                Yw = ex2_approx(Sx);
+                Z = fmaf(-f * Yw, h, Z);  // dZ = -f Y dt
+                Sx = fmaf(c, hl2, Sx);    // dY = c Y dt, Y = 2^S with S = log2(e) int c dt
+              } else if constexpr (has_f<COEF>()) {
+                Z = fmaf(-f, h, Z);       // c = 0: Y = 1
+              }
+              // dX = d dt + s dW with dW = sqrt(h) z: s sqrt(h) once, then two FMAs
+              const float ssh = s * sqh;
+              if constexpr (CV == 2) {
+                // dxi = -Y s grad u0 . dW with grad u0 from the table (Eq. 37, Sec. 4.2)
+                float gx, gy;
+                // a control variate never runs batched (pdds_assemble_batch refuses
+                // it), so the table is problem 0's, read from the launch constants:
+                // no per-step loads of the problem descriptor
+                cv_table_grad(P.prob0, xk + X, yk + Y, gx, gy);
+                XI = fmaf(-Yw * ssh, fmaf(gx, z[2 * half], gy * z[2 * half + 1]), XI);
+              }
+              if constexpr (has_drift<COEF>()) {
+                X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
+                Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
+              } else {
+                X = fmaf(ssh, z[2 * half], X);
+                Y = fmaf(ssh, z[2 * half + 1], Y);
+              }
+              ++n;
+              exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+              if constexpr (EXT && !const_sigma<COEF>()) {
+                if (exited && gmc > 0.f) exited = gm_outside<COEF>(H, S.tile(st, 0), S.tile(st, 1),
+                                                                xk, yk, X, Y, gmc, kDirect);
+              }
+              if (!exited && n >= kmax) { exited = true; trunc = true; }
             }
-            // dX = d dt + s dW with dW = sqrt(h) z: s sqrt(h) once, then two FMAs
-            const float ssh = s * sqh;
-            if constexpr (CV == 2) {
-              // dxi = -Y s grad u0 . dW with grad u0 from the table (Eq. 37, Sec. 4.2)
-              float gx, gy;
-              // a control variate never runs batched (pdds_assemble_batch refuses
-              // it), so the table is problem 0's, read from the launch constants:
-              // no per-step loads of the problem descriptor
-              cv_table_grad(P.prob0, xk + X, yk + Y, gx, gy);
-              XI = fmaf(-Yw * ssh, fmaf(gx, z[2 * half], gy * z[2 * half + 1]), XI);
-            }
-            if constexpr (has_drift<COEF>()) {
-              X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
-              Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
-            } else {
-              X = fmaf(ssh, z[2 * half], X);
-              Y = fmaf(ssh, z[2 * half + 1], Y);
-            }
-            ++n;
-            exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
-            if constexpr (EXT && !const_sigma<COEF>()) {
-              if (exited && gmc > 0.f) exited = gm_outside<COEF>(H, S.tile(st, 0), S.tile(st, 1),
-                                                              xk, yk, X, Y, gmc, P.trig_direct);
-            }
-            if (!exited && n >= kmax) { exited = true; trunc = true; }
           }
-        }
-       }
+         }
+       };
+       if (uses_angles<COEF>() && P.trig_direct) ext_calls(BoolTag<uses_angles<COEF>()>{});
+       else ext_calls(BoolTag<false>{});
       }
       const unsigned ex = __ballot_sync(kFull, alive && exited);
       const unsigned stepping = __ballot_sync(kFull, alive && !exited);
