@@ -580,14 +580,15 @@ __host__ __device__ constexpr bool uses_angles() {  // the coefficients take sin
          COEF == PDDS_COEF_POISSON_E1;
 }
 
-// Two Philox calls (four steps) of one lane's path on the naive exit: the two
-// steps of a call are taken without a branch between them -- the second one
-// starts from the first one's result and is dropped when the first one left
-// the patch or reached the step cap.  DIRECT: the coefficient sines take the
-// angle without reduction (the launch's domains allow it), a compile-time
-// choice so that the step carries no branch on it.
+// P.calls_per_check Philox calls (two steps each) of one lane's path on the
+// naive exit, between two exit checks of the warp: the two steps of a call are
+// taken without a branch between them -- the second one starts from the first
+// one's result and is dropped when the first one left the patch or reached
+// the step cap.  DIRECT: the coefficient sines take the angle without
+// reduction (the launch's domains allow it), a compile-time choice so that the
+// step carries no branch on it.
 template <int COEF, int CV, bool DIRECT>
-__device__ __forceinline__ void step_two_calls(const Stage& H, const float* tile,
+__device__ __forceinline__ void step_calls(const Stage& H, const float* tile,
                                                const KParams& P, uint32_t p, uint32_t kk,
                                                uint32_t tagw, float xk, float yk, float h,
                                                float hl2, float sqh, int kmax, float bx0,
@@ -595,7 +596,7 @@ __device__ __forceinline__ void step_two_calls(const Stage& H, const float* tile
                                                float& Y, float& Sx, float& Z, float& XI,
                                                bool& exited, bool& trunc) {
 #pragma unroll 1
-  for (int pair = 0; pair < 2 && !exited; ++pair) {
+  for (int pair = 0; pair < P.calls_per_check && !exited; ++pair) {
     const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
     float2 gA, gB;
     box_muller4(r, gA, gB);
@@ -1141,21 +1142,21 @@ __global__ void __launch_bounds__(CV == 1 ? 256 : 1024, CV == 1 ? 2 : 1)
         const Stage& H = S.st(st);
         const float* tile = S.tile(st, 0);
         if (uses_angles<COEF>() && P.trig_direct)
-          step_two_calls<COEF, CV, uses_angles<COEF>()>(H, tile, P, p, kk, tagw, xk, yk, h, hl2,
+          step_calls<COEF, CV, uses_angles<COEF>()>(H, tile, P, p, kk, tagw, xk, yk, h, hl2,
                                                         sqh, kmax, bx0, bx1, by0, by1, n, X, Y,
                                                         Sx, Z, XI, exited, trunc);
         else
-          step_two_calls<COEF, CV, false>(H, tile, P, p, kk, tagw, xk, yk, h, hl2, sqh, kmax,
+          step_calls<COEF, CV, false>(H, tile, P, p, kk, tagw, xk, yk, h, hl2, sqh, kmax,
                                           bx0, bx1, by0, by1, n, X, Y, Sx, Z, XI, exited, trunc);
       } else if (alive && !exited) {
        // extended-exit kernels (per-knot steps, Gobet-Menozzi exits, the mixed
-       // GM/EM run): two Philox pairs (four steps) between exit checks, one
+       // GM/EM run): P.calls_per_check Philox calls between exit checks, one
        // branch per step (the two-step form spills more here)
        // (the angle-reduction choice is a template constant here too)
        auto ext_calls = [&](auto direct_tag) {
         constexpr bool kDirect = decltype(direct_tag)::value;
 #pragma unroll 1
-         for (int pair = 0; pair < 2; ++pair) {
+         for (int pair = 0; pair < P.calls_per_check; ++pair) {
           if (exited) break;
           const uint4 r = kPhiloxPre ? philox_step((uint32_t)(n >> 1), ph, P.round_keys)
                             : philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);

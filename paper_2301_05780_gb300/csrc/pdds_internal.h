@@ -95,6 +95,7 @@ struct KParams {
   const int64_t* prob_unit_prefix;  // [nprob+1]
   int32_t nprob;
   int32_t exit_batch;
+  int32_t calls_per_check;          // Philox calls (two steps each) between a warp's exit checks
   int64_t total_units;
   int64_t unit_paths;
   Scratch* scratch;
