@@ -518,6 +518,8 @@ def main():
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
+    ap.add_argument("--net-engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
+                    help="tensor-core engine of the in-path network (cfg5_network)")
     ap.add_argument("--fit-data", default="knots", choices=["knots", "knots+boundary"],
                     help="what the e1 pipeline's network is fitted to: the warm-up nodal values, "
                          "plus g on the boundary")
@@ -727,6 +729,8 @@ def run_cv_network(args):
     P = pdds.Problem(w)
     from paper_2301_05780_gb300 import workloads as W
     theta = torch.tensor(W.mlp_init(), dtype=torch.float32, device="cuda")
+    engine = {"tcgen05": pdds.NET_TCGEN05, "mma_sync": pdds.NET_MMA_SYNC}[args.net_engine]
+    pdds.pdds_set_network_engine(P.ctx, engine)
     pdds.pdds_set_control_variate(P.ctx, theta)
     launch = (pdds.pdds_get_launch(P.ctx) if args.no_autotune
               else pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed))
@@ -756,8 +760,10 @@ def run_cv_network(args):
                        "dt": w.dt, "path_steps_per_step": steps / args.steps,
                        "kernel_ms": float(np.mean(kms)),
                        "launch": {"block": launch[0], "unit_paths": launch[2],
-                                  "exit_batch": launch[3]},
-                       "network": "seeded initial v_theta (2-64-64-1, SiLU)"},
+                                  "exit_batch": launch[3], "grid": st["path_grid"],
+                                  "threads": st["path_block"]},
+                       "network": "seeded initial v_theta (2-64-64-1, SiLU)",
+                       "network_engine": args.net_engine},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0

@@ -126,6 +126,8 @@ typedef struct {
   double solve_relres;      /* ||b - G u|| / ||b|| of the last pdds_solve               */
   float path_kernel_ms;     /* CUDA-event time of the last path kernel (timing on)     */
   int32_t kernel_launches;  /* kernels launched by the last assemble + solve calls      */
+  int32_t path_grid;        /* CTAs of the last path kernel                             */
+  int32_t path_block;       /* threads per CTA of the last path kernel                  */
 } pdds_stats_t;
 
 /* ------------------------------------------------------------------------ */
@@ -393,6 +395,23 @@ pdds_status pdds_mlp_eval_tc(const float* theta, const float* xy, int64_t npts, 
  * _POISSON_E1 (EINVAL otherwise, nothing changed); a staging error (ECUDA)
  * leaves no control variate attached. */
 pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
+
+/* Tensor-core engine of the in-path network of Eq. 37 (pdds_set_control_variate;
+ * the estimator, the streams and the BF16 rounding points are the same with
+ * both, so G and b differ only in the rounding of the network's products):
+ *  PDDS_NET_TCGEN05 (default): the paths of a 128-thread warpgroup step
+ *    together; at each step the 128 positions form one M = 128 tile, h1 W2^T
+ *    and g2 W2 run as tcgen05.mma (kind::f16, BF16 operands, FP32 in TMEM),
+ *    SiLU'(a1) waits in TMEM.  Launch: 128 or 256 threads per CTA (block
+ *    below 256 gives 128), at most 512 / block CTAs per SM (TMEM columns).
+ *    Naive exit only; the extended-exit calls (Gobet-Menozzi, per-knot
+ *    steps, RBF stencils) use the warp-level engine.  Each wait for a product
+ *    is bounded by max(wait limit, 1 s) (pdds_set_wait_limit).
+ *  PDDS_NET_MMA_SYNC: each warp evaluates its 32 lanes on its own with
+ *    mma.sync.m16n8k16 (BF16, FP32 accumulation in registers).
+ * Applies to later calls.  EINVAL for another value. */
+enum { PDDS_NET_MMA_SYNC = 0, PDDS_NET_TCGEN05 = 1 };
+pdds_status pdds_set_network_engine(pdds_ctx* ctx, int32_t engine);
 
 /* Tabulated control variate (Sec. 4.2: F = sigma^T grad u0 stored as an
  * interpolatory look-up table): grad_xy is a DEVICE (or host) float array

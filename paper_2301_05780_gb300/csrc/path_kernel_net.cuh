@@ -1,0 +1,464 @@
+// The path kernel with the in-path network control variate (Eq. 37; v_theta
+// of Eq. 11, 38-39) on the fifth-generation tensor cores: the paths of a
+// warpgroup (four warps, 128 lanes) step together, and at every step the
+// gradient of v_theta at their 128 positions is one M = 128 tile:
+//
+//   layer 1 (FP32 SIMT)   a1 = W1 x + b1, h1 = SiLU(a1) -> BF16 A tile in shared
+//                         memory (row = the thread's path), SiLU'(a1) -> TMEM
+//   forward (tcgen05)     D = h1 W2^T   (M = 128, N = 64, K = 64; BF16, FP32 in TMEM)
+//   output (FP32 SIMT)    g2 = w3 * SiLU'(D + b2) = dv/da2 -> the A tile (BF16)
+//   backward (tcgen05)    D = g2 W2     (same TMEM columns)
+//   input gradient        grad v = W1^T (D * SiLU'(a1))
+//
+// Thread t of a warpgroup owns TMEM lane t and row t of the tile.  One
+// elected thread issues the MMAs (kind::f16, BF16 operands as in the
+// warp-level routine of pdds_mlp.cuh) and commits them to the group's
+// mbarrier; every wait on it is bounded.  The group's four warps meet at a
+// named barrier before each product, and agree on leaving the step loop with
+// a barrier reduction, so no warp ever waits at a barrier the others do not
+// reach: every decision that ends a loop is taken for the whole group.
+//
+// Everything else -- the unit ring, the claim of paths, the Philox stream
+// and Box-Muller (one call per two steps), the EM update, the exit test and
+// its resolution -- is the warp-level code of path_kernel.cuh, unchanged, so
+// the estimator is the CV = 1 kernel's: only the rounding of the network's
+// products differs.
+#pragma once
+#include "path_kernel.cuh"
+#include "tc_sm103.cuh"
+
+namespace pdds {
+namespace {
+
+constexpr int kNetRows = 128;  // paths per warpgroup = MMA M
+constexpr int kNetH = kMlpHidden;
+
+// The network as the tensor cores read it (per CTA), and one A tile per
+// warpgroup.  BF16 tiles are K-major with the 128-byte swizzle: one 128-byte
+// row per point (64 BF16), 8-row groups 1024 bytes apart, the 16-byte chunk c
+// of row r at chunk position c ^ (r % 8).
+struct alignas(1024) NetSmem {
+  uint16_t B1[kNetH * kNetH];  // W2 as N = out x K = in
+  uint16_t B2[kNetH * kNetH];  // W2^T as N = in x K = out
+  uint16_t A[2][kNetRows * kNetH];
+  float w1x[kNetH], w1y[kNetH], b1[kNetH], b2[kNetH], w3[kNetH];
+  unsigned long long mbar[2];
+  unsigned tmem;
+};
+// + alignment slack: the dynamic shared memory is aligned by hand
+constexpr int kNetSmemBytes = (int)((sizeof(NetSmem) + 1024 + 127) / 128 * 128);
+
+__device__ __forceinline__ int net_chunk(int r, int c) {
+  return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+}
+__device__ __forceinline__ int net_elem(int r, int k) { return net_chunk(r, k >> 3) + ((k & 7) << 1); }
+
+// Named barriers 1 and 2 (0 is __syncthreads), immediate IDs: a barrier ID in
+// a register makes the compiler reserve all sixteen of the CTA's barriers.
+__device__ __forceinline__ void group_bar(int g) {
+  if (g == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+  else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+// The group's OR / AND of a predicate (a barrier with reduction: every thread
+// of the group gets the same value).
+template <int ID>
+__device__ __forceinline__ bool bar_red_or(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(ID)
+      : "memory");
+  return r != 0;
+}
+template <int ID>
+__device__ __forceinline__ bool bar_red_and(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.and.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "n"(ID)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool group_any(int g, bool v) {
+  return g == 0 ? bar_red_or<1>(v) : bar_red_or<2>(v);
+}
+__device__ __forceinline__ bool group_all(int g, bool v) {
+  return g == 0 ? bar_red_and<1>(v) : bar_red_and<2>(v);
+}
+
+// D (TMEM columns [d, d + 64)) = A B^T: four K-steps of 16 BF16 (32 bytes
+// inside the 128-byte swizzle atom).
+__device__ __forceinline__ void net_mma(unsigned d, const uint16_t* A, const uint16_t* B) {
+  constexpr uint32_t idesc = tc::idesc_bf16(kNetRows, kNetH);
+  const unsigned a = tc::smem_addr(A), b = tc::smem_addr(B);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    tc::mma_bf16(d, tc::sdesc_k128(a + kk * 32), tc::sdesc_k128(b + kk * 32), idesc, kk > 0);
+}
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) { return pack_bf16x2(lo, hi); }
+
+// Bounded wait for phase `parity` of an MMA mbarrier: one try before the
+// clock is read (a product is usually done by then).
+__device__ __forceinline__ bool net_wait(unsigned long long* bar, unsigned parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, (int)parity)) return true;
+  return tc::mbar_wait(bar, parity, limit_ns);
+}
+
+// SiLU and its slope for a pair of units on the packed FP32 pipe, rounding as
+// silu_and_slope (pdds_mlp.cuh) does per value: s = 1/2 + tanh(a/2)/2,
+// h = a s, d = s + h (1 - s).
+__device__ __forceinline__ void silu_slope2(float2 a, float2& h, float2& d) {
+  const float2 half = f2(0.5f, 0.5f);
+  const float2 ha = mul2(a, half);
+  const float2 s = fma2(f2(tanh_approx(ha.x), tanh_approx(ha.y)), half, half);
+  h = mul2(a, s);
+  d = fma2(h, fma2(s, f2(-1.0f, -1.0f), f2(1.0f, 1.0f)), s);
+}
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Whole warpgroup g (all 128 threads, converged per warp): grad v_theta at the
+// thread's point (x, y).  tm: the group's TMEM columns (D at +0, SiLU'(a1) at
+// +64), tl: the warp's TMEM lane offset.  phase: the group's mbarrier parity,
+// flipped twice.  wait_ns bounds each wait for a product.  Returns false if a
+// wait ran out (results void).  The SIMT parts work on unit pairs (f32x2).
+__device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigned tm, unsigned tl,
+                                               float x, float y, unsigned& phase,
+                                               uint64_t wait_ns, float& gx, float& gy) {
+  uint16_t* const A = N.A[g];
+  char* const Ab = reinterpret_cast<char*>(A);
+  __syncwarp();  // the tcgen05 loads and stores below are warp-aligned
+  // layer 1: h1 into row t of the A tile, SiLU'(a1) into TMEM
+  const float2 xx = f2(x, x), yy = f2(y, y);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float d[16];
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      uint32_t hp[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int u = 16 * q + 8 * c2 + 2 * j;
+        float2 h, dd;
+        silu_slope2(fma2(ld2(&N.w1x[u]), xx, fma2(ld2(&N.w1y[u]), yy, ld2(&N.b1[u]))), h, dd);
+        hp[j] = bf16x2(h.x, h.y);
+        d[8 * c2 + 2 * j] = dd.x;
+        d[8 * c2 + 2 * j + 1] = dd.y;
+      }
+      *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+    }
+    tc::tmem_st16(tm + tl + 64 + 16 * q, d);
+  }
+  tc::st_wait();
+  tc::fence_async_smem();
+  tc::fence_before();
+  group_bar(g);
+  if (t == 0) {
+    tc::fence_after();
+    net_mma(tm, A, N.B1);
+    tc::commit(&N.mbar[g]);
+  }
+  bool ok = net_wait(&N.mbar[g], phase, wait_ns);
+  phase ^= 1u;
+  tc::fence_after();
+  // dv/da2 = w3 SiLU'(a2) into the A tile (the forward product has read it)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float a2[16];
+    tc::tmem_ld16(tm + tl + 16 * q, a2);
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      uint32_t ep[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = 16 * q + 8 * c2 + 2 * j;
+        float2 h, dd;
+        silu_slope2(add2(f2(a2[8 * c2 + 2 * j], a2[8 * c2 + 2 * j + 1]), ld2(&N.b2[o])), h, dd);
+        const float2 e = mul2(ld2(&N.w3[o]), dd);
+        ep[j] = bf16x2(e.x, e.y);
+      }
+      *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(ep[0], ep[1], ep[2], ep[3]);
+    }
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  group_bar(g);
+  if (t == 0) {
+    tc::fence_after();
+    net_mma(tm, A, N.B2);
+    tc::commit(&N.mbar[g]);
+  }
+  ok = net_wait(&N.mbar[g], phase, wait_ns) && ok;
+  phase ^= 1u;
+  tc::fence_after();
+  // grad v = W1^T (dv/dh1 * SiLU'(a1)), even and odd units summed apart
+  float2 sx = f2(0.f, 0.f), sy = f2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float dh[16], s1[16];
+    tc::tmem_ld16(tm + tl + 16 * q, dh);
+    tc::tmem_ld16(tm + tl + 64 + 16 * q, s1);
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      const int u = 16 * q + j;
+      const float2 r = mul2(f2(dh[j], dh[j + 1]), f2(s1[j], s1[j + 1]));
+      sx = fma2(ld2(&N.w1x[u]), r, sx);
+      sy = fma2(ld2(&N.w1y[u]), r, sy);
+    }
+  }
+  gx = sx.x + sx.y;
+  gy = sy.x + sy.y;
+  return ok;
+}
+
+// Threads per CTA: one or two warpgroups; TMEM: 128 columns per group (64 for
+// the products, 64 for SiLU'(a1)), so at most 512 / (128 groups) CTAs per SM.
+template <int COEF, bool RECORD>
+__global__ void __launch_bounds__(2 * kNetRows, 2)
+    path_kernel_net(const __grid_constant__ KParams P) {
+  extern __shared__ __align__(128) char smem_raw[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int g = tid / kNetRows, t = tid % kNetRows;
+  const int ngroups = (int)(blockDim.x / kNetRows);
+  // 1024-byte aligned by an offset from the shared array itself, so that the
+  // compiler keeps every access in the shared state space
+  char* const nbase = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  NetSmem& N = *reinterpret_cast<NetSmem*>(nbase);
+  // the staged network (MlpSmem image): W2 and its transpose into the swizzled
+  // B tiles, the FP32 layers as they are
+  {
+    const MlpSmem& M = *reinterpret_cast<const MlpSmem*>(P.mlp);
+    const uint16_t* w2 = reinterpret_cast<const uint16_t*>(&M.W2[0][0]);
+    for (int i = tid; i < kNetH * kNetH; i += blockDim.x) {
+      const int o = i / kNetH, u = i % kNetH;
+      const uint16_t w = w2[o * kW2Pitch + u];
+      *reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(N.B1) + net_elem(o, u)) = w;
+      *reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(N.B2) + net_elem(u, o)) = w;
+    }
+    if (tid < kNetH) {
+      N.w1x[tid] = M.W1[tid][0];
+      N.w1y[tid] = M.W1[tid][1];
+      N.b1[tid] = M.b1[tid];
+      N.b2[tid] = M.b2[tid];
+      N.w3[tid] = M.w3[tid];
+    }
+  }
+  Smem S;
+  S.base = nbase + sizeof(NetSmem);
+  S.stage_bytes = P.stage_bytes;
+  S.acc_bytes = ((P.max_slots * 8) + 127) / 128 * 128;
+  S.tile_bytes = ((2 * P.tile_w * P.tile_h * 4) + 127) / 128 * 128;
+
+  __shared__ int s_live, s_qempty;
+  S.live = &s_live;
+  S.qempty = &s_qempty;
+  const int64_t total_units = P.prob_unit_prefix[P.nprob];
+  int units_done = 0;
+  if (tid == 0) {
+    s_live = 0;
+    s_qempty = 0;
+    for (int s = 0; s < 2; ++s) {
+      S.st(s).ctrl = (unsigned long long)(2u * s + 1u) << 32;  // "loading unit s"
+      S.st(s).term = 0;
+      S.st(s).tma_phase = 0;
+      mbar_init(&S.st(s).mbar);
+    }
+    for (int q = 0; q < ngroups; ++q) tc::mbar_init(&N.mbar[q]);
+  }
+  if (warp == 0) tc::tmem_alloc(&N.tmem, 128u * (unsigned)ngroups);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  bool ok = true;
+  if (warp < 2) ok = load_unit<false>(S, warp, warp, P, total_units, units_done);
+  __syncthreads();
+  const unsigned tm = N.tmem + 128u * (unsigned)g;
+  const unsigned tl = (unsigned)((warp & 3) * 32) << 16;
+  unsigned phase = 0;
+
+  // lane state (as in path_kernel)
+  bool alive = false;
+  int st = 0;
+  uint32_t p = 0, kk = 0, tagw = 0;
+  int n = 0;
+  float xk = 0.f, yk = 0.f, bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
+  float X = 0.f, Y = 0.f, Sx = 0.f, Z = 0.f, XI = 0.f;
+  unsigned long long my_steps = 0, my_paths = 0, my_trunc = 0, my_clamp = 0;
+  int want = 0;
+  const uint64_t wait_ns = P.wait_ns;
+  // a product takes microseconds; its wait gets the launch's limit, but never
+  // less than a second, so that no MMA can still be running when the kernel
+  // gives up and releases its tensor memory
+  const uint64_t mma_wait_ns = wait_ns > 1000000000ull ? wait_ns : 1000000000ull;
+  uint64_t idle_since = 0;
+
+  for (;;) {
+    // every exit from this loop is decided for the whole group
+    if (!group_all(g, ok)) break;
+    // ---- hand new paths to idle lanes (per warp, never waits) --------------
+    unsigned idle = __ballot_sync(kFull, !alive);
+    for (int guard = 0; idle && guard < 64; ++guard) {
+      Stage& H = S.st(want & 1);
+      const unsigned ss = ctrl_state(&H.ctrl);
+      if ((int)(ss >> 1) > want) { ++want; continue; }
+      if ((ss & 1u) || (int)(ss >> 1) < want) break;
+      if (H.term) { ++want; continue; }
+      const int cnt = __popc(idle);
+      const int leader = __ffs(idle) - 1;
+      unsigned long long c = 0;
+      if (lane == leader) c = atomicAdd(&H.ctrl, (unsigned long long)cnt);
+      c = __shfl_sync(kFull, c, leader);
+      __threadfence_block();
+      const unsigned sa = (unsigned)(c >> 32);
+      if (sa & 1u) break;
+      const int base = (int)(unsigned)(c & 0xffffffffull);
+      const int pend = H.p_end;
+      __threadfence_block();
+      if (ctrl_state(&H.ctrl) != sa) {
+        want = max(want, (int)(sa >> 1) + 1);
+        continue;
+      }
+      want = max(want, (int)(sa >> 1));
+      const int got = max(0, min(cnt, pend - base));
+      const int rank = __popc(idle & ((1u << lane) - 1u));
+      if (!alive && rank < got) {
+        alive = true;
+        st = want & 1;
+        p = (uint32_t)(base + rank);
+        kk = (uint32_t)H.k;
+        tagw = (uint32_t)H.tag;
+        xk = H.kd.xk; yk = H.kd.yk;
+        bx0 = H.kd.box[0]; bx1 = H.kd.box[1]; by0 = H.kd.box[2]; by1 = H.kd.box[3];
+        n = 0; X = 0.f; Y = 0.f; Sx = 0.f; Z = 0.f; XI = 0.f;
+      }
+      if (base + cnt >= pend) ++want;
+      idle = __ballot_sync(kFull, !alive);
+    }
+    if (!group_any(g, alive)) {
+      // no path in the whole group: done once the queue is empty and no unit
+      // of this CTA is loaded or loading, else wait (bounded) for a unit
+      const int qe = *(volatile int*)S.qempty;
+      __threadfence_block();
+      const bool fin = qe && *(volatile int*)S.live == 0;
+      if (group_all(g, fin)) break;
+      if (idle_since == 0) idle_since = global_ns();
+      if (group_any(g, global_ns() - idle_since > wait_ns)) {
+        if (t == 0) atomicExch(&P.scratch->error, (int)PDDS_ETIMEOUT);
+        break;
+      }
+      __nanosleep(256);
+      continue;
+    }
+    idle_since = 0;
+
+    // ---- step until a warp of the group has gathered enough exits ---------
+    const float h = P.h, sqh = P.sqh;
+    const float hl2 = h * 1.44269504088896341f;
+    const int kmax = (int)min(P.kmax, (int64_t)0x7fffffff);
+    bool exited = false, trunc = false;
+    for (;;) {
+      const bool go = alive && !exited;
+      float z[4] = {0.f, 0.f, 0.f, 0.f};
+      if (go) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 1), p, kk, tagw), P.round_keys);
+        box_muller(r.x, r.y, z[0], z[1]);
+        box_muller(r.z, r.w, z[2], z[3]);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float gx, gy;
+        if (!net_grad_group(N, g, t, tm, tl, xk + X, yk + Y, phase, mma_wait_ns, gx, gy)) ok = false;
+        if (go && !exited) {
+          const Stage& H = S.st(st);
+          float s, ddx, ddy, c, f;
+          coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.trig_direct,
+                       s, ddx, ddy, c, f);
+          const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
+          float Yw = 1.0f;
+          if constexpr (has_c<COEF>()) Yw = ex2_approx(Sx);
+          if constexpr (has_f<COEF>()) Z = fmaf(-f * Yw, h, Z);
+          if constexpr (has_c<COEF>()) Sx = fmaf(c, hl2, Sx);
+          XI = fmaf(-Yw * s, fmaf(gx, dWx, gy * dWy), XI);  // dxi = -Y s grad v . dW (Eq. 37)
+          const float ssh = s * sqh;
+          X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
+          Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
+          ++n;
+          exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+          if (!exited && n >= kmax) { exited = true; trunc = true; }
+        }
+      }
+      const unsigned ex = __ballot_sync(kFull, alive && exited);
+      const unsigned stepping = __ballot_sync(kFull, alive && !exited);
+      if (group_any(g, stepping == 0 || __popc(ex) >= P.exit_batch || !ok)) break;
+    }
+    if (!ok && t == 0) atomicExch(&P.scratch->error, (int)PDDS_ETIMEOUT);
+
+    // ---- resolve the exits (Eq. 22-25, corner rule of Sec. 3.3) -----------
+    const bool leaving = alive && exited;
+    ExitResult E;
+    if (leaving)
+      E = resolve_exit<COEF, RECORD, 1, false>(S, P, st, xk, yk, X, Y, Sx, Z, XI, trunc, bx0,
+                                                 bx1, by0, by1, 0.f, false);
+    if (leaving) {
+      my_steps += (unsigned long long)n;
+      my_paths += 1;
+      my_trunc += (E.flags & 1);
+      my_clamp += (E.flags >> 1) & 1;
+      if constexpr (RECORD) write_record(S, P, st, kk, p, n, E, XI, false);
+      atomicAdd(&S.st(st).bsum, E.bc);
+    }
+    // warp-aggregated completion counts per stage; the warp that finishes a
+    // unit flushes it and loads the next one (bounded waits only)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const unsigned m = __ballot_sync(kFull, leaving && st == s);
+      if (m == 0) continue;
+      __syncwarp();
+      __threadfence_block();
+      int fin = 0;
+      if (lane == 0) {
+        Stage& H = S.st(s);
+        const int old = atomicAdd(&H.done, __popc(m));
+        fin = (old + __popc(m) == H.total);
+      }
+      fin = __shfl_sync(kFull, fin, 0);
+      if (fin) {
+        const int q = (int)(ctrl_state(&S.st(s).ctrl) >> 1);
+        flush_unit(S, s, P);
+        if (!load_unit<false>(S, s, q + 2, P, total_units, units_done)) ok = false;
+        if (lane == 0) atomicSub(S.live, 1);
+        __syncwarp();
+      }
+    }
+    if (leaving) alive = false;
+  }
+
+  my_steps = warp_sum_u64(my_steps);
+  my_paths = warp_sum_u64(my_paths);
+  my_trunc = warp_sum_u64(my_trunc);
+  my_clamp = warp_sum_u64(my_clamp);
+  if (lane == 0) {
+    atomicAdd(&P.scratch->steps, my_steps);
+    atomicAdd(&P.scratch->paths, my_paths);
+    atomicAdd(&P.scratch->truncated, my_trunc);
+    atomicAdd(&P.scratch->clamped, my_clamp);
+    atomicAdd(&P.scratch->units, (unsigned long long)units_done);
+  }
+  // TMEM back once both groups are done with it
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(N.tmem, 128u * (unsigned)ngroups);
+  }
+}
+
+}  // namespace
+}  // namespace pdds

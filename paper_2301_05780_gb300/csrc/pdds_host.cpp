@@ -14,6 +14,12 @@
 #include "pdds.h"
 #include "pdds_internal.h"
 
+namespace pdds {
+// Dynamic shared memory of the tcgen05 network kernel ahead of its unit ring
+// (pdds_path_net.cu).
+size_t net_smem_bytes();
+}  // namespace pdds
+
 using pdds::KnotDesc;
 using pdds::ProbDesc;
 
@@ -224,6 +230,7 @@ struct pdds_ctx {
   int64_t unit_paths = 4096;
   int64_t k_max = 0;
   uint32_t tag = 0;  // Philox tag (fourth counter word) of single-problem calls
+  int net_engine = PDDS_NET_TCGEN05;  // tensor-core engine of the in-path network
   int batch_calls = 0;  // > 0: Philox calls between exit checks of a batched launch
   bool timing = false;
   bool timing_pending = false;  // ev0/ev1 recorded around a path kernel, time not read yet
@@ -451,8 +458,10 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   const double kmax_eff = ext && c->d_hknot && c->h_min < dt ? (double)kmax * dt / c->h_min
                                                              : (double)kmax;
   kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * kmax_eff);
-  const int cv = nprob == 1 ? c->cv_mode : 0;
-  kp.mlp = cv == 1 ? c->d_mlp : nullptr;
+  // cv 3: the in-path network on tcgen05 (warpgroup kernel, naive exit only)
+  int cv = nprob == 1 ? c->cv_mode : 0;
+  if (cv == 1 && !ext && c->net_engine == PDDS_NET_TCGEN05) cv = 3;
+  kp.mlp = cv == 1 || cv == 3 ? c->d_mlp : nullptr;
   {
     // the largest |coordinate| of the launch's domains (problem 0 here, the
     // batch caller gives the bound over all of them) decides whether the
@@ -467,17 +476,26 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
     kp.trig_direct = B <= lim ? 1 : 0;
   }
   // the network step is ~10x heavier: wait bounds scale with it
-  if (cv == 1 && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
-  // network kernels keep the staged network at the start of dynamic shared memory
-  const size_t smem = 2 * sbytes + (cv == 1 ? round_up(pdds::mlp_image_bytes(), 128) : 0);
+  if ((cv == 1 || cv == 3) && c->wait_s <= 0) kp.wait_ns = (uint64_t)(10e9 + 40000.0 * kmax_eff);
+  // network kernels keep the staged network at the start of dynamic shared
+  // memory (the tcgen05 kernel: its swizzled operand tiles)
+  const size_t smem = 2 * sbytes + (cv == 1   ? round_up(pdds::mlp_image_bytes(), 128)
+                                    : cv == 3 ? pdds::net_smem_bytes()
+                                              : 0);
   CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, ext, smem));
-  const int block = cv == 1 ? std::min(c->block, 256) : c->block;  // network: <= 256 threads
+  // network: <= 256 threads; the tcgen05 kernel takes one or two warpgroups
+  const int block = cv == 1 ? std::min(c->block, 256) : cv == 3 ? (c->block >= 256 ? 256 : 128)
+                                                                : c->block;
   int per_sm = c->ctas_per_sm;
   if (per_sm <= 0) {
     CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, ext, block, smem, &per_sm));
     if (per_sm <= 0) return fail(c, PDDS_EINVAL, "launch: block/shared memory too large");
   }
+  // tcgen05 kernel: 128 TMEM columns per warpgroup, 512 per SM
+  if (cv == 3) per_sm = std::min(per_sm, 512 / block);
   const int grid = c->num_sms * per_sm;
+  c->st.path_grid = grid;
+  c->st.path_block = block;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
   CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, ext, kp, grid, block, smem, stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
@@ -804,6 +822,14 @@ pdds_status pdds_set_philox_tag(pdds_ctx* c, uint32_t tag) {
   return PDDS_OK;
 }
 
+pdds_status pdds_set_network_engine(pdds_ctx* c, int32_t engine) {
+  if (!c) return fail(nullptr, PDDS_EINVAL, "set_network_engine: NULL context");
+  if (engine != PDDS_NET_MMA_SYNC && engine != PDDS_NET_TCGEN05)
+    return fail(c, PDDS_EINVAL, "set_network_engine: unknown engine");
+  c->net_engine = engine;
+  return PDDS_OK;
+}
+
 pdds_status pdds_set_wait_limit(pdds_ctx* c, double seconds) {
   if (!c) return fail(nullptr, PDDS_EINVAL, "set_wait_limit: NULL context");
   if (!(seconds >= 0) || seconds > 1e6) return fail(c, PDDS_EINVAL, "set_wait_limit: need 0 <= s <= 1e6");
@@ -829,8 +855,11 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   static std::map<Key, Shape> cache;
   // xk: the extended-exit kernel (GM scheme or per-knot steps) is a different kernel
   const int xk = (c->scheme == PDDS_SCHEME_GM ? 1 : 0) + (c->d_hknot ? 2 : 0);
-  const Key key{c->device, c->coef_id, c->cv_mode, xk, c->grid.Hx, c->grid.Hy, c->grid.m,
-                c->grid.ext, n_paths};
+  // the in-path network on tcgen05 (naive exit) is its own kernel too
+  const bool net_tc = c->cv_mode == 1 && xk == 0 && c->interp != PDDS_INTERP_RBF &&
+                      c->net_engine == PDDS_NET_TCGEN05;
+  const Key key{c->device, c->coef_id, net_tc ? 3 : c->cv_mode, xk, c->grid.Hx, c->grid.Hy,
+                c->grid.m, c->grid.ext, n_paths};
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
@@ -883,7 +912,8 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   for (int bl : blocks)
     for (int un : units)
       for (int ba : batches)
-        if (!(c->cv_mode == 1 && bl > 256)) shapes.push_back(Shape{bl, un, ba});
+        if (!(c->cv_mode == 1 && bl > 256) && !(net_tc && bl < 128))
+          shapes.push_back(Shape{bl, un, ba});
   auto time_shape = [&](const Shape& sh, const int64_t* N, int64_t Nu, float& ms) {
     c->block = sh.block;
     c->unit_paths = sh.unit;

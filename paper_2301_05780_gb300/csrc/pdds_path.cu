@@ -4,6 +4,8 @@
 // pdds_path_{em,cv,cvt,ext,ext_cv,ext_cvt}.cu so that they compile in parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "pdds.h"
@@ -91,16 +93,19 @@ void* path_kernel_cvt(int coef, bool rec);
 void* path_kernel_ext(int coef, bool rec);
 void* path_kernel_ext_cv(int coef, bool rec);
 void* path_kernel_ext_cvt(int coef, bool rec);
+void* path_kernel_net_tc(int coef, bool rec);  // cv 3: the network on tcgen05 (pdds_path_net.cu)
 
 namespace {
 void* pick(int coef, bool rec, int cv, bool ext) {
   if (ext) {
+    if (cv == 3) return nullptr;
     if (cv == 1) return path_kernel_ext_cv(coef, rec);
     if (cv == 2) return path_kernel_ext_cvt(coef, rec);
     return path_kernel_ext(coef, rec);
   }
   if (cv == 1) return path_kernel_cv(coef, rec);
   if (cv == 2) return path_kernel_cvt(coef, rec);
+  if (cv == 3) return path_kernel_net_tc(coef, rec);
   return path_kernel_em(coef, rec);
 }
 }  // namespace
@@ -119,13 +124,40 @@ cudaError_t path_kernel_occupancy(int coef, bool rec, int cv, bool ext, int bloc
                                   int* ctas) {
   void* fn = pick(coef, rec, cv, ext);
   if (!fn) return cudaErrorInvalidValue;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+  if (cv != 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
+  // The tcgen05 network kernel: the occupancy query answers one CTA per SM
+  // for it, while registers, shared memory (large carve-out) and tensor
+  // memory admit more (measured: four 128-thread CTAs per SM run 2.3x faster
+  // than one), so the count is taken from those three limits directly.
+  cudaFuncAttributes fa;
+  int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  const int regs = (fa.numRegs + 7) / 8 * 8;  // allocated per warp in 256-register steps
+  const int by_regs = regs_sm / (regs * block);
+  const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + (size_t)smem_res);
+  const int by_tmem = 512 / block;  // 128 TMEM columns per 128-thread warpgroup
+  *ctas = std::max(0, std::min(std::min(by_regs, by_smem), by_tmem));
+  return cudaSuccess;
 }
 
 cudaError_t set_path_kernel_smem(int coef, bool rec, int cv, bool ext, size_t smem) {
   void* fn = pick(coef, rec, cv, ext);
   if (!fn) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the tcgen05 network kernel (~55 KB per CTA) needs the large shared-memory
+  // carve-out for two CTAs per SM
+  if (e == cudaSuccess && cv == 3)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 cudaError_t launch_unit_prefix(const int64_t* N, int64_t n, int64_t C, int64_t* up, int64_t* pp,

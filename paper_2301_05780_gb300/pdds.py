@@ -52,7 +52,8 @@ class pdds_stats_t(C.Structure):
     _fields_ = [("path_steps", C.c_int64), ("paths", C.c_int64), ("truncated", C.c_int64),
                 ("clamped", C.c_int64), ("units", C.c_int64), ("device_error", C.c_int32),
                 ("solve_iters", C.c_int32), ("solve_relres", C.c_double),
-                ("path_kernel_ms", C.c_float), ("kernel_launches", C.c_int32)]
+                ("path_kernel_ms", C.c_float), ("kernel_launches", C.c_int32),
+                ("path_grid", C.c_int32), ("path_block", C.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("steps", "<i4"), ("side_flags", "<i4"), ("col_a", "<i4"),
@@ -78,6 +79,7 @@ _SIGS = {
     "pdds_set_timing": (C.c_int, [_P, C.c_int32]),
     "pdds_set_wait_limit": (C.c_int, [_P, C.c_double]),
     "pdds_set_philox_tag": (C.c_int, [_P, C.c_uint32]),
+    "pdds_set_network_engine": (C.c_int, [_P, C.c_int32]),
     "pdds_autotune": (C.c_int, [_P, C.c_int64, C.c_double, C.c_uint64, _P]),
     "pdds_assemble": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P]),
     "pdds_assemble_records": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_uint64, _P, _P, _P,
@@ -226,6 +228,15 @@ def pdds_set_philox_tag(ctx, tag: int):
     """Philox tag of later single-problem calls on ctx (problem i of a batch
     draws with tag i)."""
     _check(lib().pdds_set_philox_tag(ctx, C.c_uint32(int(tag))), ctx)
+
+
+NET_MMA_SYNC, NET_TCGEN05 = 0, 1
+
+
+def pdds_set_network_engine(ctx, engine: int):
+    """Tensor-core engine of the in-path network: NET_TCGEN05 (default,
+    warpgroup tiles of 128 paths) or NET_MMA_SYNC (warp-level)."""
+    _check(lib().pdds_set_network_engine(ctx, C.c_int32(int(engine))), ctx)
 
 
 def pdds_set_timing(ctx, on: bool):

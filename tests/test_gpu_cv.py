@@ -128,12 +128,15 @@ def _cv_workload(N, H=3, m=4):
     return w
 
 
-def test_cv_assembly_parity_with_oracle(orc, oracle_theta):
+@pytest.mark.parametrize("engine", [pdds.NET_TCGEN05, pdds.NET_MMA_SYNC],
+                         ids=["tcgen05", "mma_sync"])
+def test_cv_assembly_parity_with_oracle(orc, oracle_theta, engine):
     """Same streams, same (oracle-fitted) theta: G as in the plain parity
     protocol; b within 1e-4 plus 2 % of sum |xi| (xi carries the BF16 network
-    error)."""
+    error).  Both tensor-core engines of the in-path network."""
     w = _cv_workload(400)
     P = pdds.Problem(w)
+    pdds.pdds_set_network_engine(P.ctx, engine)
     pdds.pdds_set_control_variate(P.ctx, dev32(oracle_theta))
     rec = P.records_buffer()
     P.assemble(records=rec)

@@ -128,9 +128,11 @@ def _grad_table(n):
     return np.stack([gx, gy], axis=-1).astype(np.float32)
 
 
-def _cfg5_check(orc, cv, oracle_theta=None):
+def _cfg5_check(orc, cv, oracle_theta=None, engine=None):
     w = W.config5()
     P = pdds.Problem(w)
+    if engine is not None:
+        pdds.pdds_set_network_engine(P.ctx, engine)
     O = orc.Problem(w.grid, w.coef_id, w.params)
     tab = None
     if cv == "table":
@@ -183,8 +185,10 @@ def test_config5_tabulated_cv_full_size_rows(orc):
     _cfg5_check(orc, "table")
 
 
-def test_config5_network_cv_full_size_rows(orc, oracle_theta):
+@pytest.mark.parametrize("engine", [pdds.NET_TCGEN05, pdds.NET_MMA_SYNC],
+                         ids=["tcgen05", "mma_sync"])
+def test_config5_network_cv_full_size_rows(orc, oracle_theta, engine):
     """Config 5 with the in-path network control variate (Eq. 37, BF16
     tensor-core gradient on the GPU, FP64 on the oracle, the same
-    oracle-fitted parameters on both sides)."""
-    _cfg5_check(orc, "network", oracle_theta)
+    oracle-fitted parameters on both sides), with each tensor-core engine."""
+    _cfg5_check(orc, "network", oracle_theta, engine)
