@@ -41,12 +41,19 @@ struct alignas(1024) NetSmem {
   uint16_t B1[kNetH * kNetH];  // W2 as N = out x K = in
   uint16_t B2[kNetH * kNetH];  // W2^T as N = in x K = out
   uint16_t A[2][kNetRows * kNetH];
-  float w1x[kNetH], w1y[kNetH], b1[kNetH], b2[kNetH], w3[kNetH];
   unsigned long long mbar[2];
   unsigned tmem;
 };
 // + alignment slack: the dynamic shared memory is aligned by hand
 constexpr int kNetSmemBytes = (int)((sizeof(NetSmem) + 1024 + 127) / 128 * 128);
+
+// The network's FP32 vectors, halved (W1[:, 0]/2, W1[:, 1]/2, b1/2, b2/2,
+// w3/2; the SiLU algebra below works with a/2), as a kernel parameter: every
+// thread reads the same value at the same time, so they are served from the
+// constant bank instead of shared memory.
+struct NetWeights {
+  float w1x[kNetH], w1y[kNetH], b1[kNetH], b2[kNetH], w3[kNetH];
+};
 
 __device__ __forceinline__ int net_chunk(int r, int c) {
   return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
@@ -109,15 +116,13 @@ __device__ __forceinline__ bool net_wait(unsigned long long* bar, unsigned parit
   return tc::mbar_wait(bar, parity, limit_ns);
 }
 
-// SiLU and its slope for a pair of units on the packed FP32 pipe, rounding as
-// silu_and_slope (pdds_mlp.cuh) does per value: s = 1/2 + tanh(a/2)/2,
-// h = a s, d = s + h (1 - s).
-__device__ __forceinline__ void silu_slope2(float2 a, float2& h, float2& d) {
-  const float2 half = f2(0.5f, 0.5f);
-  const float2 ha = mul2(a, half);
-  const float2 s = fma2(f2(tanh_approx(ha.x), tanh_approx(ha.y)), half, half);
-  h = mul2(a, s);
-  d = fma2(h, fma2(s, f2(-1.0f, -1.0f), f2(1.0f, 1.0f)), s);
+// SiLU through t = tanh(a/2), for a pair of units on the packed FP32 pipe:
+// with a' = a/2 (the network's weights and biases halved, an exact scaling),
+//   SiLU(a) = a (1 + t)/2 = a' (1 + t),
+//   SiLU'(a) = (1 + t)/2 + a (1 - t^2)/4 = (1 + t + a' (1 - t^2)) / 2.
+__device__ __forceinline__ float2 tanh2(float2 a) { return f2(tanh_approx(a.x), tanh_approx(a.y)); }
+__device__ __forceinline__ float2 one_minus_sq(float2 t) {
+  return fma2(t, f2(-t.x, -t.y), f2(1.0f, 1.0f));
 }
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -126,9 +131,10 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 // +64), tl: the warp's TMEM lane offset.  phase: the group's mbarrier parity,
 // flipped twice.  wait_ns bounds each wait for a product.  Returns false if a
 // wait ran out (results void).  The SIMT parts work on unit pairs (f32x2).
-__device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigned tm, unsigned tl,
-                                               float x, float y, unsigned& phase,
-                                               uint64_t wait_ns, float& gx, float& gy) {
+__device__ __forceinline__ bool net_grad_group(NetSmem& N, const NetWeights& W, int g, int t,
+                                               unsigned tm, unsigned tl, float x, float y,
+                                               unsigned& phase, uint64_t wait_ns, float& gx,
+                                               float& gy) {
   uint16_t* const A = N.A[g];
   char* const Ab = reinterpret_cast<char*>(A);
   __syncwarp();  // the tcgen05 loads and stores below are warp-aligned
@@ -143,11 +149,13 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigne
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int u = 16 * q + 8 * c2 + 2 * j;
-        float2 h, dd;
-        silu_slope2(fma2(ld2(&N.w1x[u]), xx, fma2(ld2(&N.w1y[u]), yy, ld2(&N.b1[u]))), h, dd);
+        const float2 a = fma2(ld2(&W.w1x[u]), xx, fma2(ld2(&W.w1y[u]), yy, ld2(&W.b1[u])));  // a1/2
+        const float2 t = tanh2(a);
+        const float2 h = fma2(a, t, a);                                                // SiLU(a1)
+        const float2 s = add2(fma2(a, one_minus_sq(t), t), f2(1.0f, 1.0f));            // 2 SiLU'(a1)
         hp[j] = bf16x2(h.x, h.y);
-        d[8 * c2 + 2 * j] = dd.x;
-        d[8 * c2 + 2 * j + 1] = dd.y;
+        d[8 * c2 + 2 * j] = s.x;
+        d[8 * c2 + 2 * j + 1] = s.y;
       }
       *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
     }
@@ -176,9 +184,11 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigne
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int o = 16 * q + 8 * c2 + 2 * j;
-        float2 h, dd;
-        silu_slope2(add2(f2(a2[8 * c2 + 2 * j], a2[8 * c2 + 2 * j + 1]), ld2(&N.b2[o])), h, dd);
-        const float2 e = mul2(ld2(&N.w3[o]), dd);
+        // a2/2: the forward product runs on W2/2
+        const float2 a = add2(f2(a2[8 * c2 + 2 * j], a2[8 * c2 + 2 * j + 1]), ld2(&W.b2[o]));
+        const float2 t = tanh2(a);
+        const float2 w = ld2(&W.w3[o]);  // w3/2
+        const float2 e = fma2(w, fma2(a, one_minus_sq(t), t), w);  // w3 SiLU'(a2)
         ep[j] = bf16x2(e.x, e.y);
       }
       *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(ep[0], ep[1], ep[2], ep[3]);
@@ -195,7 +205,8 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigne
   ok = net_wait(&N.mbar[g], phase, wait_ns) && ok;
   phase ^= 1u;
   tc::fence_after();
-  // grad v = W1^T (dv/dh1 * SiLU'(a1)), even and odd units summed apart
+  // grad v = W1^T (dv/dh1 * SiLU'(a1)) = (W1/2)^T (dv/dh1 * 2 SiLU'(a1)), even
+  // and odd units summed apart
   float2 sx = f2(0.f, 0.f), sy = f2(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -206,8 +217,8 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigne
     for (int j = 0; j < 16; j += 2) {
       const int u = 16 * q + j;
       const float2 r = mul2(f2(dh[j], dh[j + 1]), f2(s1[j], s1[j + 1]));
-      sx = fma2(ld2(&N.w1x[u]), r, sx);
-      sy = fma2(ld2(&N.w1y[u]), r, sy);
+      sx = fma2(ld2(&W.w1x[u]), r, sx);
+      sy = fma2(ld2(&W.w1y[u]), r, sy);
     }
   }
   gx = sx.x + sx.y;
@@ -219,7 +230,7 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, int g, int t, unsigne
 // the products, 64 for SiLU'(a1)), so at most 512 / (128 groups) CTAs per SM.
 template <int COEF, bool RECORD>
 __global__ void __launch_bounds__(2 * kNetRows, 2)
-    path_kernel_net(const __grid_constant__ KParams P) {
+    path_kernel_net(const __grid_constant__ KParams P, const __grid_constant__ NetWeights W) {
   extern __shared__ __align__(128) char smem_raw[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -230,23 +241,18 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
   // compiler keeps every access in the shared state space
   char* const nbase = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   NetSmem& N = *reinterpret_cast<NetSmem*>(nbase);
-  // the staged network (MlpSmem image): W2 and its transpose into the swizzled
-  // B tiles, the FP32 layers as they are
+  // the staged network (MlpSmem image): W2 / 2 (forward: the product gives
+  // a2/2, exactly) and W2^T into the swizzled B tiles (the FP32 layers come
+  // as the kernel parameter W)
   {
     const MlpSmem& M = *reinterpret_cast<const MlpSmem*>(P.mlp);
     const uint16_t* w2 = reinterpret_cast<const uint16_t*>(&M.W2[0][0]);
     for (int i = tid; i < kNetH * kNetH; i += blockDim.x) {
       const int o = i / kNetH, u = i % kNetH;
       const uint16_t w = w2[o * kW2Pitch + u];
-      *reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(N.B1) + net_elem(o, u)) = w;
+      const uint16_t wh = (uint16_t)(bf16x2(0.5f * __uint_as_float((uint32_t)w << 16), 0.f) & 0xffffu);
+      *reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(N.B1) + net_elem(o, u)) = wh;
       *reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(N.B2) + net_elem(u, o)) = w;
-    }
-    if (tid < kNetH) {
-      N.w1x[tid] = M.W1[tid][0];
-      N.w1y[tid] = M.W1[tid][1];
-      N.b1[tid] = M.b1[tid];
-      N.b2[tid] = M.b2[tid];
-      N.w3[tid] = M.w3[tid];
     }
   }
   Smem S;
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         float gx, gy;
-        if (!net_grad_group(N, g, t, tm, tl, xk + X, yk + Y, phase, mma_wait_ns, gx, gy)) ok = false;
+        if (!net_grad_group(N, W, g, t, tm, tl, xk + X, yk + Y, phase, mma_wait_ns, gx, gy)) ok = false;
         if (go && !exited) {
           const Stage& H = S.st(st);
           float s, ddx, ddy, c, f;

@@ -15,9 +15,12 @@
 #include "pdds_internal.h"
 
 namespace pdds {
-// Dynamic shared memory of the tcgen05 network kernel ahead of its unit ring
-// (pdds_path_net.cu).
+// Dynamic shared memory of the tcgen05 network kernel ahead of its unit ring,
+// and its launch with the network's FP32 vectors (host, 5 x 64: W1[:, 0],
+// W1[:, 1], b1, b2, w3) as a kernel parameter (pdds_path_net.cu).
 size_t net_smem_bytes();
+cudaError_t launch_path_kernel_net(int coef, bool rec, const KParams& kp, const float* w,
+                                   int grid, int block, size_t smem, cudaStream_t stream);
 }  // namespace pdds
 
 using pdds::KnotDesc;
@@ -231,6 +234,7 @@ struct pdds_ctx {
   int64_t k_max = 0;
   uint32_t tag = 0;  // Philox tag (fourth counter word) of single-problem calls
   int net_engine = PDDS_NET_TCGEN05;  // tensor-core engine of the in-path network
+  float net_w[5 * 64] = {};  // the attached network's W1[:, 0], W1[:, 1], b1, b2, w3
   int batch_calls = 0;  // > 0: Philox calls between exit checks of a batched launch
   bool timing = false;
   bool timing_pending = false;  // ev0/ev1 recorded around a path kernel, time not read yet
@@ -497,7 +501,11 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   c->st.path_grid = grid;
   c->st.path_block = block;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
-  CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, ext, kp, grid, block, smem, stream));
+  if (cv == 3)
+    CK(c, pdds::launch_path_kernel_net(coef_id, rec != nullptr, kp, c->net_w, grid, block, smem,
+                                       stream));
+  else
+    CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, ext, kp, grid, block, smem, stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
   return PDDS_OK;
 }
@@ -972,6 +980,18 @@ pdds_status pdds_set_control_variate(pdds_ctx* c, const float* theta) {
   if (!c->d_mlp) CK(c, cudaMalloc(&c->d_mlp, pdds::mlp_image_bytes()));
   CK(c, pdds::mlp_stage(theta, c->d_mlp, nullptr));
   CK(c, cudaDeviceSynchronize());
+  {
+    // host copy of the FP32 vectors (kernel parameter of the tcgen05 engine)
+    std::vector<float> th(PDDS_MLP_NPARAM);
+    CK(c, cudaMemcpy(th.data(), theta, sizeof(float) * PDDS_MLP_NPARAM, cudaMemcpyDefault));
+    for (int u = 0; u < 64; ++u) {
+      c->net_w[u] = th[2 * u];
+      c->net_w[64 + u] = th[2 * u + 1];
+      c->net_w[128 + u] = th[128 + u];   // b1
+      c->net_w[192 + u] = th[4288 + u];  // b2
+      c->net_w[256 + u] = th[4352 + u];  // w3
+    }
+  }
   c->cv_mode = 1;
   return PDDS_OK;
 }

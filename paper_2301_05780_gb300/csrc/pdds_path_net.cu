@@ -28,4 +28,22 @@ void* path_kernel_net_tc(int coef, bool rec) {
 
 size_t net_smem_bytes() { return (size_t)kNetSmemBytes; }
 
+// w: host array of the network's FP32 vectors, W1[:, 0], W1[:, 1], b1, b2, w3
+// (64 each), passed halved, by value, as the kernel's second parameter.
+cudaError_t launch_path_kernel_net(int coef, bool rec, const KParams& kp, const float* w,
+                                   int grid, int block, size_t smem, cudaStream_t stream) {
+  void* fn = path_kernel_net_tc(coef, rec);
+  if (!fn) return cudaErrorInvalidValue;
+  NetWeights W;
+  for (int u = 0; u < kNetH; ++u) {
+    W.w1x[u] = 0.5f * w[u];
+    W.w1y[u] = 0.5f * w[kNetH + u];
+    W.b1[u] = 0.5f * w[2 * kNetH + u];
+    W.b2[u] = 0.5f * w[3 * kNetH + u];
+    W.w3[u] = 0.5f * w[4 * kNetH + u];
+  }
+  void* args[] = {const_cast<KParams*>(&kp), &W};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
+}
+
 }  // namespace pdds
