@@ -518,6 +518,9 @@ def main():
                     help="control variate of the e1 pipeline: tabulated grad u0 or the network")
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
+    ap.add_argument("--launch", default=None,
+                    help="cfg5_network: fixed launch shape 'block,unit_paths,exit_batch' "
+                         "(no autotune; profiling runs)")
     ap.add_argument("--net-engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
                     help="tensor-core engine of the in-path network (cfg5_network)")
     ap.add_argument("--fit-data", default="knots", choices=["knots", "knots+boundary"],
@@ -732,7 +735,10 @@ def run_cv_network(args):
     engine = {"tcgen05": pdds.NET_TCGEN05, "mma_sync": pdds.NET_MMA_SYNC}[args.net_engine]
     pdds.pdds_set_network_engine(P.ctx, engine)
     pdds.pdds_set_control_variate(P.ctx, theta)
-    launch = (pdds.pdds_get_launch(P.ctx) if args.no_autotune
+    if args.launch:
+        blk, un, ba = (int(v) for v in args.launch.split(","))
+        pdds.pdds_set_launch(P.ctx, blk, 0, un, ba)
+    launch = (pdds.pdds_get_launch(P.ctx) if args.no_autotune or args.launch
               else pdds.pdds_autotune(P.ctx, w.n_paths, w.dt, w.seed))
     pdds.pdds_set_timing(P.ctx, True)
     stream = torch.cuda.current_stream()

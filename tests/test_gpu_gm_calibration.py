@@ -223,8 +223,12 @@ def test_calibration_moments_parity(orc, oracle_theta, use_cv, k_cap, knot_steps
         # a network fitted by the oracle itself: nothing the oracle reads comes
         # from the library
         theta = torch.tensor(oracle_theta, dtype=torch.float32, device="cuda")
-    # GPU: calibration moments, plus the two record passes it is made of
+    # GPU: calibration moments, plus the two record passes it is made of.
+    # The calibration's mixed GM/EM run is an extended-exit kernel, which
+    # evaluates the network with the warp-level engine; the naive-exit record
+    # pass below takes the same engine, so that the two agree to the last bit.
     P = _problem(w, EM, h_per_knot=h_k, theta=theta)
+    pdds.pdds_set_network_engine(P.ctx, pdds.NET_MMA_SYNC)
     if tab is not None:
         pdds.pdds_set_control_variate_grid(P.ctx, torch.tensor(tab, device="cuda"))
     mom = torch.empty(n, 8, dtype=torch.float64, device="cuda")
