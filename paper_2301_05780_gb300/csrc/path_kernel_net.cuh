@@ -126,15 +126,15 @@ __device__ __forceinline__ float2 one_minus_sq(float2 t) {
 }
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
-// Whole warpgroup g (all 128 threads, converged per warp): grad v_theta at the
-// thread's point (x, y).  tm: the group's TMEM columns (D at +0, SiLU'(a1) at
-// +64), tl: the warp's TMEM lane offset.  phase: the group's mbarrier parity,
-// flipped twice.  wait_ns bounds each wait for a product.  Returns false if a
-// wait ran out (results void).  The SIMT parts work on unit pairs (f32x2).
-__device__ __forceinline__ bool net_grad_group(NetSmem& N, const NetWeights& W, int g, int t,
-                                               unsigned tm, unsigned tl, float x, float y,
-                                               unsigned& phase, uint64_t wait_ns, float& gx,
-                                               float& gy) {
+// grad v_theta at the thread's point (x, y), in two parts so that the caller
+// can work while the forward product runs: net_grad_start (layer 1, then one
+// thread issues the forward product) and net_grad_finish.  Whole warpgroup g
+// (all 128 threads, converged per warp).  tm: the group's TMEM columns (D at
+// +0, 2 SiLU'(a1) at +64), tl: the warp's TMEM lane offset.  phase: the
+// group's mbarrier parity, flipped twice by net_grad_finish, whose wait_ns
+// bounds each wait for a product.  The SIMT parts work on unit pairs (f32x2).
+__device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, int g, int t,
+                                               unsigned tm, unsigned tl, float x, float y) {
   uint16_t* const A = N.A[g];
   char* const Ab = reinterpret_cast<char*>(A);
   __syncwarp();  // the tcgen05 loads and stores below are warp-aligned
@@ -170,6 +170,16 @@ __device__ __forceinline__ bool net_grad_group(NetSmem& N, const NetWeights& W, 
     net_mma(tm, A, N.B1);
     tc::commit(&N.mbar[g]);
   }
+}
+
+// Second part of the evaluation (whole warpgroup): wait for the forward
+// product, then layer 2, the backward product and the input gradient.
+// Returns false if a wait ran out (results void).
+__device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W, int g, int t,
+                                                unsigned tm, unsigned tl, unsigned& phase,
+                                                uint64_t wait_ns, float& gx, float& gy) {
+  uint16_t* const A = N.A[g];
+  char* const Ab = reinterpret_cast<char*>(A);
   bool ok = net_wait(&N.mbar[g], phase, wait_ns);
   phase ^= 1u;
   tc::fence_after();
@@ -377,28 +387,38 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
         box_muller(r.x, r.y, z[0], z[1]);
         box_muller(r.z, r.w, z[2], z[3]);
       }
-#pragma unroll
+      // one copy of the network code for both steps of the Philox call
+#pragma unroll 1
       for (int half = 0; half < 2; ++half) {
-        float gx, gy;
-        if (!net_grad_group(N, W, g, t, tm, tl, xk + X, yk + Y, phase, mma_wait_ns, gx, gy)) ok = false;
-        if (go && !exited) {
+        const float za = half ? z[2] : z[0], zb = half ? z[3] : z[1];
+        // the network at the step's starting point; while the forward product
+        // runs, the step itself (the path does not depend on the network)
+        net_grad_start(N, W, g, t, tm, tl, xk + X, yk + Y);
+        const bool stepping_now = go && !exited;
+        float fac = 0.f, dWx = 0.f, dWy = 0.f;
+        if (stepping_now) {
           const Stage& H = S.st(st);
           float s, ddx, ddy, c, f;
           coeffs<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk + X, yk + Y, X, Y, P.trig_direct,
                        s, ddx, ddy, c, f);
-          const float dWx = sqh * z[2 * half], dWy = sqh * z[2 * half + 1];
+          dWx = sqh * za;
+          dWy = sqh * zb;
           float Yw = 1.0f;
           if constexpr (has_c<COEF>()) Yw = ex2_approx(Sx);
           if constexpr (has_f<COEF>()) Z = fmaf(-f * Yw, h, Z);
           if constexpr (has_c<COEF>()) Sx = fmaf(c, hl2, Sx);
-          XI = fmaf(-Yw * s, fmaf(gx, dWx, gy * dWy), XI);  // dxi = -Y s grad v . dW (Eq. 37)
+          fac = -Yw * s;
           const float ssh = s * sqh;
-          X = fmaf(ssh, z[2 * half], fmaf(ddx, h, X));
-          Y = fmaf(ssh, z[2 * half + 1], fmaf(ddy, h, Y));
+          X = fmaf(ssh, za, fmaf(ddx, h, X));
+          Y = fmaf(ssh, zb, fmaf(ddy, h, Y));
           ++n;
           exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
           if (!exited && n >= kmax) { exited = true; trunc = true; }
         }
+        float gx, gy;
+        if (!net_grad_finish(N, W, g, t, tm, tl, phase, mma_wait_ns, gx, gy)) ok = false;
+        // dxi = -Y s grad v . dW at the step's starting point (Eq. 37)
+        if (stepping_now) XI = fmaf(fac, fmaf(gx, dWx, gy * dWy), XI);
       }
       const unsigned ex = __ballot_sync(kFull, alive && exited);
       const unsigned stepping = __ballot_sync(kFull, alive && !exited);
