@@ -357,6 +357,26 @@ pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target, i
                            int32_t steps, double lr, double* loss_history_host,
                            void* cuda_stream);
 
+/* The same loss gradient and training on the fifth-generation tensor cores
+ * (the fit of Phase I, Sec. 4.3): tiles of 128 points, one 256-thread CTA
+ * per tile at a time (two warpgroups, each half of the hidden units; at most
+ * two CTAs per SM: ~107 KB of shared memory and 256 TMEM columns each); the
+ * forward product h1 W2^T, the backward product
+ * g2 W2 and the weight gradient [g2 | g1]^T [h1 | x | y | 1] (contracted over
+ * the tile's points, accumulated in TMEM over the CTA's tiles) run as
+ * tcgen05.mma kind::f16 with BF16 operands and FP32 accumulation; the rest
+ * is FP32.  The loss and the gradient carry the BF16 rounding of the
+ * products' operands (within 1e-2 of the FP64 loss and gradient norm).
+ * Arguments, the Adam step, scratch, graph replay and synchronisation as for
+ * pdds_mlp_loss_grad / pdds_mlp_train.  A bounded tensor-core wait (2 s) that
+ * runs out makes that step's loss NaN (loss, loss_history_host).
+ * Errors: EINVAL, ECUDA. */
+pdds_status pdds_mlp_loss_grad_tc(const float* theta, const float* xy, const float* target,
+                                  int64_t npts, float* grad, double* loss, void* cuda_stream);
+pdds_status pdds_mlp_train_tc(float* theta, const float* xy, const float* target, int64_t npts,
+                              int32_t steps, double lr, double* loss_history_host,
+                              void* cuda_stream);
+
 /* v_theta and grad v_theta at npts DEVICE points with the in-path evaluation
  * (64x64 layer on the tensor cores with BF16 operands and FP32 accumulation;
  * the rest FP32).  v (nullable) [npts], grad_xy [npts][2].  Synchronizes. */

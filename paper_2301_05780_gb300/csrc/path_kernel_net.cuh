@@ -150,9 +150,9 @@ __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, 
       for (int j = 0; j < 4; ++j) {
         const int u = 16 * q + 8 * c2 + 2 * j;
         const float2 a = fma2(ld2(&W.w1x[u]), xx, fma2(ld2(&W.w1y[u]), yy, ld2(&W.b1[u])));  // a1/2
-        const float2 t = tanh2(a);
-        const float2 h = fma2(a, t, a);                                                // SiLU(a1)
-        const float2 s = add2(fma2(a, one_minus_sq(t), t), f2(1.0f, 1.0f));            // 2 SiLU'(a1)
+        const float2 th = tanh2(a);
+        const float2 h = fma2(a, th, a);                                               // SiLU(a1)
+        const float2 s = add2(fma2(a, one_minus_sq(th), th), f2(1.0f, 1.0f));          // 2 SiLU'(a1)
         hp[j] = bf16x2(h.x, h.y);
         d[8 * c2 + 2 * j] = s.x;
         d[8 * c2 + 2 * j + 1] = s.y;
@@ -196,9 +196,9 @@ __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W,
         const int o = 16 * q + 8 * c2 + 2 * j;
         // a2/2: the forward product runs on W2/2
         const float2 a = add2(f2(a2[8 * c2 + 2 * j], a2[8 * c2 + 2 * j + 1]), ld2(&W.b2[o]));
-        const float2 t = tanh2(a);
+        const float2 th = tanh2(a);
         const float2 w = ld2(&W.w3[o]);  // w3/2
-        const float2 e = fma2(w, fma2(a, one_minus_sq(t), t), w);  // w3 SiLU'(a2)
+        const float2 e = fma2(w, fma2(a, one_minus_sq(th), th), w);  // w3 SiLU'(a2)
         ep[j] = bf16x2(e.x, e.y);
       }
       *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(ep[0], ep[1], ep[2], ep[3]);

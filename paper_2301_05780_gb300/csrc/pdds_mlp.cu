@@ -18,12 +18,11 @@
 
 #include "pdds.h"
 #include "pdds_internal.h"
+#include "mlp_train.h"
 #include "pdds_mlp.cuh"
 
 namespace pdds {
 namespace {
-
-constexpr int kOffW1 = 0, kOffB1 = 128, kOffW2 = 192, kOffB2 = 4288, kOffW3 = 4352, kOffB3 = 4416;
 
 // ------------------------------------------------------------- training
 // One launch = one full-batch gradient of the loss (1/N) sum_p (v(x_p) -
@@ -70,29 +69,6 @@ static_assert(offsetof(TrainSmem, G2) == offsetof(TrainSmem, H1) + sizeof(float)
               "g2 follows h1");
 static_assert(5 * (kTrainThreads / 32) * 64 <= 2 * kTileP * kLd,
               "column-sum staging fits in h1 and g2");
-
-// Step state of a training run (device, zeroed before the first step).
-struct TrainState {
-  unsigned count;  // CTAs done with the current launch
-  int t;           // index of the next launch
-  double p1, p2;   // beta1^t, beta2^t for launch t >= 1
-};
-
-struct TrainArgs {
-  float* theta;     // parameters (training: read by launch 0, written by the last)
-  const float* xy;
-  const float* tgt;
-  int64_t npts;
-  float scale;      // 2 / N: d loss / d v
-  double inv_n;     // 1 / N
-  float* grad;      // gradient: one buffer (gradient only) or three (training)
-  double* loss;     // loss; training: the loss history, indexed by the step
-  // training only
-  float *th2, *m2, *v2;  // [2][kMlpParams] each
-  TrainState* st;
-  int steps;
-  float lr, beta1, beta2, eps;
-};
 
 // Parameter i of theta (layout W1[64][2], b1, W2[64][64], b2, w3, b3) into
 // the shared-memory image.
@@ -484,17 +460,38 @@ cudaError_t train_grid(int64_t npts, unsigned* grid) {
   *grid = (unsigned)std::min<int64_t>(tiles, 2 * (int64_t)sms);
   return cudaSuccess;
 }
-}  // namespace
 
-extern "C" pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, const float* target,
-                                          int64_t npts, float* grad, double* loss,
-                                          void* cuda_stream) {
+// Kernel and launch shape of a training engine: 0 the FP32 SIMT kernel, 1 the
+// tensor-core kernel.
+cudaError_t train_config(int engine, bool adam, int64_t npts, const void** fn, unsigned* grid,
+                         unsigned* threads, size_t* smem) {
+  if (engine == 1) return train_tc_launch_config(adam, npts, fn, grid, threads, smem);
+  cudaError_t e = train_grid(npts, grid);
+  if (e != cudaSuccess) return e;
+  *fn = adam ? reinterpret_cast<const void*>(&mlp_train_kernel<true>)
+             : reinterpret_cast<const void*>(&mlp_train_kernel<false>);
+  *threads = kTrainThreads;
+  *smem = kTrainSmemBytes;
+  return cudaSuccess;
+}
+
+cudaError_t launch_train(const void* fn, unsigned grid, unsigned threads, size_t smem,
+                         const TrainArgs& a, cudaStream_t s) {
+  void* args[] = {const_cast<TrainArgs*>(&a)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+}
+
+pdds_status loss_grad_impl(int engine, const char* name, const float* theta, const float* xy,
+                           const float* target, int64_t npts, float* grad, double* loss,
+                           void* cuda_stream) {
   if (!theta || !xy || !target || !grad || !loss || npts < 1)
-    return mlp_fail(PDDS_EINVAL, "mlp_loss_grad: NULL pointer or npts < 1");
+    return mlp_fail(PDDS_EINVAL, std::string(name) + ": NULL pointer or npts < 1");
   (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  unsigned grid = 0;
-  MCK(train_grid(npts, &grid));
+  const void* fn = nullptr;
+  unsigned grid = 0, threads = 0;
+  size_t smem = 0;
+  MCK(train_config(engine, false, npts, &fn, &grid, &threads, &smem));
   MCK(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), s));
   MCK(cudaMemsetAsync(loss, 0, sizeof(double), s));
   TrainArgs a{};
@@ -506,20 +503,36 @@ extern "C" pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, c
   a.inv_n = 1.0 / (double)npts;
   a.grad = grad;
   a.loss = loss;
-  mlp_train_kernel<false><<<grid, kTrainThreads, kTrainSmemBytes, s>>>(a);
-  MCK(cudaGetLastError());
+  MCK(launch_train(fn, grid, threads, smem, a, s));
   return PDDS_OK;
 }
+}  // namespace
 
-extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target,
-                                      int64_t npts, int32_t steps, double lr,
-                                      double* loss_history_host, void* cuda_stream) {
+extern "C" pdds_status pdds_mlp_loss_grad(const float* theta, const float* xy, const float* target,
+                                          int64_t npts, float* grad, double* loss,
+                                          void* cuda_stream) {
+  return loss_grad_impl(0, "mlp_loss_grad", theta, xy, target, npts, grad, loss, cuda_stream);
+}
+
+extern "C" pdds_status pdds_mlp_loss_grad_tc(const float* theta, const float* xy,
+                                             const float* target, int64_t npts, float* grad,
+                                             double* loss, void* cuda_stream) {
+  return loss_grad_impl(1, "mlp_loss_grad_tc", theta, xy, target, npts, grad, loss, cuda_stream);
+}
+
+namespace {
+pdds_status train_impl(int engine, const char* name, float* theta, const float* xy,
+                       const float* target, int64_t npts, int32_t steps, double lr,
+                       double* loss_history_host, void* cuda_stream) {
   if (!theta || !xy || !target || npts < 1 || steps < 1 || !(lr > 0))
-    return mlp_fail(PDDS_EINVAL, "mlp_train: NULL pointer, npts < 1, steps < 1 or lr <= 0");
+    return mlp_fail(PDDS_EINVAL,
+                    std::string(name) + ": NULL pointer, npts < 1, steps < 1 or lr <= 0");
   (void)cudaGetLastError();
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  unsigned grid = 0;
-  MCK(train_grid(npts, &grid));
+  const void* fn = nullptr;
+  unsigned grid = 0, threads = 0;
+  size_t smem = 0;
+  MCK(train_config(engine, true, npts, &fn, &grid, &threads, &smem));
   // scratch: three gradients and two each of theta, m, v (FP32), the step
   // state, the loss history
   const size_t fbytes = 9 * kMlpParams * sizeof(float);
@@ -566,9 +579,9 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
       const int launches = steps + 1;
       const int chunk = std::min(launches, 64);
       if ((q = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) return q;
-      for (int k = 0; k < chunk; ++k)
-        mlp_train_kernel<true><<<grid, kTrainThreads, kTrainSmemBytes, cs>>>(a);
-      cudaError_t lq = cudaGetLastError();
+      cudaError_t lq = cudaSuccess;
+      for (int k = 0; k < chunk && lq == cudaSuccess; ++k)
+        lq = launch_train(fn, grid, threads, smem, a, cs);
       q = cudaStreamEndCapture(cs, &graph);
       if (lq) return lq;
       if (q) return q;
@@ -594,8 +607,23 @@ extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float
   };
   cudaError_t e = run();
   cudaFree(buf);
-  if (e != cudaSuccess) return mlp_cuda(e, "mlp_train");
+  if (e != cudaSuccess) return mlp_cuda(e, name);
   return PDDS_OK;
+}
+}  // namespace
+
+extern "C" pdds_status pdds_mlp_train(float* theta, const float* xy, const float* target,
+                                      int64_t npts, int32_t steps, double lr,
+                                      double* loss_history_host, void* cuda_stream) {
+  return train_impl(0, "mlp_train", theta, xy, target, npts, steps, lr, loss_history_host,
+                    cuda_stream);
+}
+
+extern "C" pdds_status pdds_mlp_train_tc(float* theta, const float* xy, const float* target,
+                                         int64_t npts, int32_t steps, double lr,
+                                         double* loss_history_host, void* cuda_stream) {
+  return train_impl(1, "mlp_train_tc", theta, xy, target, npts, steps, lr, loss_history_host,
+                    cuda_stream);
 }
 
 extern "C" pdds_status pdds_mlp_eval(const float* theta, const float* xy, int64_t npts, float* v,

@@ -96,6 +96,8 @@ _SIGS = {
     "pdds_solve_noalloc": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, _P, _P]),
     "pdds_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "pdds_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
+    "pdds_mlp_loss_grad_tc": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "pdds_mlp_train_tc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P]),
     "pdds_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "pdds_mlp_eval_tc": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "pdds_boundary_samples": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
@@ -355,21 +357,25 @@ def pdds_solve_noalloc(G, b, u, rtol=1e-12, maxit=2000, stream=None, n=None):
 MLP_NPARAM = 4417
 
 
-def pdds_mlp_loss_grad(theta, xy, target, stream=None):
-    """(loss, grad) of the MSE fit of v_theta (device float32 tensors)."""
+def pdds_mlp_loss_grad(theta, xy, target, stream=None, engine="fp32"):
+    """(loss, grad) of the MSE fit of v_theta (device float32 tensors);
+    engine "fp32" (FP32 SIMT kernel) or "tc" (BF16 products on tcgen05)."""
     import torch
     grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=theta.device)
     loss = torch.empty(1, dtype=torch.float64, device=theta.device)
-    _check(lib().pdds_mlp_loss_grad(_dptr(theta), _dptr(xy), _dptr(target), target.numel(),
-                                    _dptr(grad), _dptr(loss), _stream(stream)))
+    fn = lib().pdds_mlp_loss_grad_tc if engine == "tc" else lib().pdds_mlp_loss_grad
+    _check(fn(_dptr(theta), _dptr(xy), _dptr(target), target.numel(), _dptr(grad), _dptr(loss),
+              _stream(stream)))
     return loss, grad
 
 
-def pdds_mlp_train(theta, xy, target, steps, lr=3e-3, stream=None):
-    """Adam on theta in place; returns the loss history (numpy)."""
+def pdds_mlp_train(theta, xy, target, steps, lr=3e-3, stream=None, engine="fp32"):
+    """Adam on theta in place; returns the loss history (numpy).  engine as
+    for pdds_mlp_loss_grad."""
     hist = np.zeros(int(steps))
-    _check(lib().pdds_mlp_train(_dptr(theta), _dptr(xy), _dptr(target), target.numel(),
-                                int(steps), float(lr), hist.ctypes.data, _stream(stream)))
+    fn = lib().pdds_mlp_train_tc if engine == "tc" else lib().pdds_mlp_train
+    _check(fn(_dptr(theta), _dptr(xy), _dptr(target), target.numel(), int(steps), float(lr),
+              hist.ctypes.data, _stream(stream)))
     return hist
 
 

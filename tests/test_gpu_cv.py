@@ -95,6 +95,76 @@ def test_mlp_train_follows_oracle_adam(orc):
     assert np.abs(d_g - d_o).max() <= 2 * steps * lr + 1e-6
 
 
+@pytest.mark.parametrize("npts", [1000, 40017])
+def test_mlp_loss_grad_tc_matches_oracle(orc, npts):
+    """The tensor-core trainer's loss and gradient (BF16 operands of the three
+    products, FP32 accumulation) against the oracle's FP64 ones, within 1e-2
+    of the loss and of the gradient's norm (the stated BF16 bound).  40,017
+    points: more 128-point tiles than CTAs (two per SM), so CTAs accumulate
+    several tiles in TMEM; the last tile is ragged."""
+    rng = np.random.default_rng(21 + npts)
+    th32 = (W.mlp_init() * rng.uniform(0.5, 1.5, orc.MLP_NPARAM)).astype(np.float32)
+    xy = rng.uniform(-1, 1, size=(npts, 2)).astype(np.float32)
+    tgt = (np.cos(2 * xy[:, 0]) + xy[:, 1] ** 2).astype(np.float32)
+    loss_o, g_o = orc.mlp_loss_grad(th32.astype(np.float64), xy.astype(np.float64),
+                                    tgt.astype(np.float64))
+    loss, g = pdds.pdds_mlp_loss_grad(dev32(th32), dev32(xy), dev32(tgt), engine="tc")
+    assert abs(loss.item() - loss_o) <= 1e-2 * loss_o, (loss.item(), loss_o)
+    gg = g.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(gg - g_o) / np.linalg.norm(g_o)
+    assert rel <= 1e-2, rel
+    # every block of parameters, not only the norm: W1, b1, W2, b2, w3, b3
+    for a, b in ((0, 128), (128, 192), (192, 4288), (4288, 4352), (4352, 4416), (4416, 4417)):
+        assert np.linalg.norm(gg[a:b] - g_o[a:b]) <= 3e-2 * np.linalg.norm(g_o[a:b]) + 1e-9, (a, b)
+
+
+def test_mlp_train_tc_follows_oracle_adam(orc):
+    """pdds_mlp_train_tc against the oracle's FP64 gradient and Adam step, 12
+    steps on 1013 points: the loss history within 1e-2, and the parameter moves
+    where the gradient stays well above rounding within 0.1 lr (a relative
+    gradient error d changes an Adam step by at most about 2 d lr; 12 steps at
+    d = 2^-8, the BF16 rounding, give 0.09 lr)."""
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(0, 1, size=(1013, 2)).astype(np.float32)
+    tgt = (np.sin(3 * xy[:, 0]) * xy[:, 1]).astype(np.float32)
+    th0 = W.mlp_init().astype(np.float32).astype(np.float64)
+    steps, lr = 12, 3e-3
+    th, m, v = th0.copy(), np.zeros_like(th0), np.zeros_like(th0)
+    hist_o, grads = [], []
+    for t in range(1, steps + 1):
+        loss, g = orc.mlp_loss_grad(th, xy.astype(np.float64), tgt.astype(np.float64))
+        hist_o.append(loss)
+        grads.append(np.abs(g))
+        orc.adam_step(th, g, m, v, t, lr=lr)
+    thg = dev32(th0)
+    hist = pdds.pdds_mlp_train(thg, dev32(xy), dev32(tgt), steps=steps, lr=lr, engine="tc")
+    np.testing.assert_allclose(hist, hist_o, rtol=1e-2)
+    G = np.array(grads)
+    robust = (G > 1e-2 * G.max(axis=1, keepdims=True)).all(axis=0)
+    assert robust.mean() > 0.15, robust.mean()  # the oracle's own gradients: ~1000 parameters
+    d_o = th - th0
+    d_g = thg.cpu().numpy().astype(np.float64) - th0
+    err = np.abs(d_g - d_o)[robust].max()
+    assert err <= 0.1 * lr, err
+    assert np.abs(d_g - d_o).max() <= 2 * steps * lr + 1e-6
+
+
+def test_mlp_train_tc_fits_like_fp32():
+    """1500 Adam steps on 8192 points of the manufactured u with each trainer:
+    the tensor-core one lowers the loss by more than 100x and ends within 2x
+    of the FP32 one."""
+    rng = np.random.default_rng(2)
+    xy = rng.uniform(0, 1, size=(8192, 2))
+    tgt = dev32(u_exact(xy[:, 0], xy[:, 1]))
+    out = {}
+    for eng in ("fp32", "tc"):
+        th = dev32(W.mlp_init())
+        out[eng] = pdds.pdds_mlp_train(th, dev32(xy), tgt, steps=1500, lr=3e-3, engine=eng)
+    assert np.all(np.isfinite(out["tc"]))
+    assert out["tc"][-1] < 1e-2 * out["tc"][0], (out["tc"][0], out["tc"][-1])
+    assert out["tc"][-1] < 2 * out["fp32"][-1], (out["tc"][-1], out["fp32"][-1])
+
+
 def test_mlp_inpath_eval_matches_oracle(orc, oracle_theta):
     """The warp-batched BF16 MMA evaluation (also used inside the path kernel)
     against the FP64 network on the same (oracle-fitted) parameters: 1e-2 of
