@@ -523,6 +523,8 @@ def main():
                          "(no autotune; profiling runs)")
     ap.add_argument("--net-engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
                     help="tensor-core engine of the in-path network (cfg5_network)")
+    ap.add_argument("--train-engine", default="tc", choices=["fp32", "tc"],
+                    help="training kernel of the network fits (e1, cfg5): FP32 SIMT or tcgen05")
     ap.add_argument("--fit-data", default="knots", choices=["knots", "knots+boundary"],
                     help="what the e1 pipeline's network is fitted to: the warm-up nodal values, "
                          "plus g on the boundary")
@@ -783,7 +785,7 @@ def run_cv_study(args):
     torch.cuda.set_device(0)
     w = workload("cfg5")
     n_plain = args.paths or w.n_paths
-    res = cv.study(w, n_plain)
+    res = cv.study(w, n_plain, train_engine=args.train_engine)
     plain = res["plain"]
     line = {"metric": METRIC, "value": plain["path_steps"] / (plain["kernel_ms"] * 1e-3),
             "unit": "path-steps/s", "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -898,7 +900,7 @@ def run_e1(args):
     x = w.extra
     kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
               rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps,
-              boundary_samples=args.fit_data == "knots+boundary")
+              boundary_samples=args.fit_data == "knots+boundary", train_engine=args.train_engine)
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []
@@ -922,7 +924,7 @@ def run_e1(args):
                        "n0": kw["n0"], "h0": x["h0"], "n_job": x["n_job"],
                        "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
                        "control_variate": args.cv, "train_steps": args.train_steps,
-                       "fit_data": args.fit_data,
+                       "fit_data": args.fit_data, "train_engine": args.train_engine,
                        "note": "path-steps simulated in the three phases (the calibration's "
                                "mixed GM/EM paths once, to their naive exits)"},
             "pipeline": {

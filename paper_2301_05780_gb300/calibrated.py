@@ -36,13 +36,16 @@ def _sync_ms(fn):
     return out, 1e3 * (time.perf_counter() - t0)
 
 
-def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev, boundary=None):
+def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev, boundary=None,
+                engine: str = "tc"):
     """Fits v_theta to the nodal values u0 at the knots xy (and, given
     boundary = (xy_b, g_b), to the boundary data there) with the library's
     Adam kernels, on inputs scaled to [-1, 1]^2 and targets standardised, and
     folds both affine maps into the first and last layers, so that the
     returned theta (device float32) evaluates v in the problem's coordinates:
-      W1' = W1 / s,  b1' = b1 - W1 c / s,  w3' = sd w3,  b3' = sd b3 + mean."""
+      W1' = W1 / s,  b1' = b1 - W1 c / s,  w3' = sd w3,  b3' = sd b3 + mean.
+    engine: the training kernel, "fp32" (FP32 SIMT) or "tc" (BF16 products on
+    the tcgen05 tensor cores)."""
     import torch
     c = np.array([(grid["x0"] + grid["x1"]) / 2, (grid["y0"] + grid["y1"]) / 2])
     s = np.array([(grid["x1"] - grid["x0"]) / 2, (grid["y1"] - grid["y0"]) / 2])
@@ -54,7 +57,7 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev, boundary=None):
     xy_n = torch.tensor((xy - c) / s, dtype=torch.float32, device=dev)
     t_n = torch.tensor((u - mean) / sd, dtype=torch.float32, device=dev)
     theta = torch.tensor(W.mlp_init(), dtype=torch.float32, device=dev)
-    hist = pdds.pdds_mlp_train(theta, xy_n, t_n, steps=steps, lr=lr)
+    hist = pdds.pdds_mlp_train(theta, xy_n, t_n, steps=steps, lr=lr, engine=engine)
     th = theta.double().cpu().numpy()
     H = 64
     W1 = th[0:2 * H].reshape(H, 2).copy()
@@ -70,7 +73,8 @@ def fit_network(xy, u0, grid: dict, steps: int, lr: float, dev, boundary=None):
 def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | None = None,
         h0p: float | None = None, control_variate: bool = True, train_steps: int = 1500,
         lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
-        rbf_shape: float = 0.0, cv_kind: str = "table", boundary_samples: bool = True) -> dict:
+        rbf_shape: float = 0.0, cv_kind: str = "table", boundary_samples: bool = True,
+        train_engine: str = "tc") -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
     and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
     instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
@@ -79,6 +83,7 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     evaluates v_theta in the path (two 64 x 64 products per step).
     boundary_samples: the fit also sees g at the boundary points of the
     lattice (pdds_boundary_samples), where u is known exactly.
+    train_engine: the fit's training kernel ("fp32" or "tc", fit_network).
     Returns the nodal solutions of Phases I and III, the calibration (h_i,
     N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and
     path-step counts."""
@@ -116,7 +121,8 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
         def fit():
             bnd = (pdds.pdds_boundary_samples(P.ctx, w.grid["Hx"] * w.grid["m"], dev)
                    if boundary_samples else None)
-            return fit_network(xy, u0, w.grid, train_steps, lr, dev, boundary=bnd)
+            return fit_network(xy, u0, w.grid, train_steps, lr, dev, boundary=bnd,
+                               engine=train_engine)
         (theta, hist), tfit = _sync_ms(fit)
         if cv_kind == "network":
             pdds.pdds_set_control_variate(P.ctx, theta)
@@ -124,7 +130,8 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
         else:
             _, ttab = _sync_ms(lambda: tabulate_gradient(P.ctx, theta, w.grid, dev))
         out["fit"] = {"ms": tfit + ttab, "steps": train_steps, "final_loss": float(hist[-1]),
-                      "cv_kind": cv_kind, "boundary_samples": boundary_samples}
+                      "cv_kind": cv_kind, "boundary_samples": boundary_samples,
+                      "train_engine": train_engine}
 
     # Phase II: mixed GM/EM calibration and Eq. 40-41
     mom = torch.empty(n, pdds.CAL_NMOM, dtype=torch.float64, device=dev)

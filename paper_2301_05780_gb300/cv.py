@@ -40,11 +40,13 @@ def _ms(fn):
 
 
 def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float = 3e-3,
-                        seed_offset: int = 7919, max_points: int = 16384) -> CVResult:
+                        seed_offset: int = 7919, max_points: int = 16384,
+                        engine: str = "tc") -> CVResult:
     """Phase I on P's grid with n0 paths per knot, then fit v_theta to u0 at
     (at most max_points, seeded) knots and to g at the lattice's boundary
     points: u0 is smooth at the network's scale, so a subset of the knots
-    trains it as well as every knot for a fraction of the cost."""
+    trains it as well as every knot for a fraction of the cost.  engine: the
+    training kernel ("fp32" or "tc", pdds_mlp_train)."""
     import torch
     w = P.w
     dev = P.dev
@@ -68,7 +70,7 @@ def fit_control_variate(P: pdds.Problem, n0: int, steps: int = 2000, lr: float =
     hist = [None]
 
     def train():
-        hist[0] = pdds.pdds_mlp_train(theta, xy, u0, steps=steps, lr=lr)
+        hist[0] = pdds.pdds_mlp_train(theta, xy, u0, steps=steps, lr=lr, engine=engine)
 
     train_ms = _ms(train)
     return CVResult(theta, warm_ms, train_ms, hist[0])
@@ -103,7 +105,7 @@ def _assemble_solve(P: pdds.Problem, N: int, seed: int):
 
 
 def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 1000,
-          ref_factor: int = 4) -> dict:
+          ref_factor: int = 4, train_engine: str = "tc") -> dict:
     """Time to equal interfacial statistical error, plain vs control variate.
 
     Statistical error is measured as RMS(u - u_ref) over the knots, where u_ref
@@ -118,7 +120,7 @@ def study(w: W.Workload, n_plain: int, n0: int = 1000, train_steps: int = 1000,
     out["launch_plain"] = pdds.pdds_autotune(P.ctx, n_plain, w.dt, w.seed)
     t_plain, u_plain, steps_plain, k_plain = _assemble_solve(P, n_plain, w.seed)
     # control variate: warm-up, fit, production
-    fit = fit_control_variate(P, n0, steps=train_steps)
+    fit = fit_control_variate(P, n0, steps=train_steps, engine=train_engine)
     pdds.pdds_set_control_variate(P.ctx, fit.theta)
     # variance-reduction probe on a small budget decides the production N
     t_probe, u_probe, _, _ = _assemble_solve(P, max(n0, 256), w.seed + 3)
