@@ -424,9 +424,9 @@ pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
  *    and g2 W2 run as tcgen05.mma (kind::f16, BF16 operands, FP32 in TMEM),
  *    SiLU'(a1) waits in TMEM.  Launch: 128 or 256 threads per CTA (block
  *    below 256 gives 128), at most 512 / block CTAs per SM (TMEM columns).
- *    Naive exit only; the extended-exit calls (Gobet-Menozzi, per-knot
- *    steps, RBF stencils) use the warp-level engine.  Each wait for a product
- *    is bounded by max(wait limit, 1 s) (pdds_set_wait_limit).
+ *    Both exits (naive and extended: Gobet-Menozzi, per-knot steps, RBF
+ *    stencils, the calibration's mixed run).  Each wait for a product is
+ *    bounded by max(wait limit, 1 s) (pdds_set_wait_limit).
  *  PDDS_NET_MMA_SYNC: each warp evaluates its 32 lanes on its own with
  *    mma.sync.m16n8k16 (BF16, FP32 accumulation in registers).
  * Applies to later calls.  EINVAL for another value. */

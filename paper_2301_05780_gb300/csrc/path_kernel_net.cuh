@@ -238,7 +238,7 @@ __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W,
 
 // Threads per CTA: one or two warpgroups; TMEM: 128 columns per group (64 for
 // the products, 64 for SiLU'(a1)), so at most 512 / (128 groups) CTAs per SM.
-template <int COEF, bool RECORD>
+template <int COEF, bool RECORD, bool EXT>
 __global__ void __launch_bounds__(2 * kNetRows, 2)
     path_kernel_net(const __grid_constant__ KParams P, const __grid_constant__ NetWeights W) {
   extern __shared__ __align__(128) char smem_raw[];
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
   __syncthreads();
   tc::fence_after();
   bool ok = true;
-  if (warp < 2) ok = load_unit<false>(S, warp, warp, P, total_units, units_done);
+  if (warp < 2) ok = load_unit<EXT>(S, warp, warp, P, total_units, units_done);
   __syncthreads();
   const unsigned tm = N.tmem + 128u * (unsigned)g;
   const unsigned tl = (unsigned)((warp & 3) * 32) << 16;
@@ -308,6 +308,13 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
   float X = 0.f, Y = 0.f, Sx = 0.f, Z = 0.f, XI = 0.f;
   unsigned long long my_steps = 0, my_paths = 0, my_trunc = 0, my_clamp = 0;
   int want = 0;
+  // EXT: the knot's step, its square root, step cap and Gobet-Menozzi shift
+  // per unit of |s|; the mixed GM/EM run of the calibration (records kernels
+  // with the extended exit) as in path_kernel
+  constexpr bool kMixed = EXT && RECORD;
+  bool gm_phase = false, pend_em = false, pend_tr = false;
+  int64_t kmax_l = 0;
+  float h_l = 0.f, sqh_l = 0.f, gmc = 0.f;
   const uint64_t wait_ns = P.wait_ns;
   // a product takes microseconds; its wait gets the launch's limit, but never
   // less than a second, so that no MMA can still be running when the kernel
@@ -352,6 +359,16 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
         tagw = (uint32_t)H.tag;
         xk = H.kd.xk; yk = H.kd.yk;
         bx0 = H.kd.box[0]; bx1 = H.kd.box[1]; by0 = H.kd.box[2]; by1 = H.kd.box[3];
+        if constexpr (EXT) {
+          h_l = H.h; sqh_l = H.sqh; kmax_l = H.kmax; gmc = H.gmc;
+          // the cheap exit test uses the box moved by the largest shift
+          const float dm = gmc * sigma_bound<COEF>(H);
+          bx0 += dm; bx1 -= dm; by0 += dm; by1 -= dm;
+        }
+        if constexpr (kMixed) {
+          gm_phase = P.mixed != 0;
+          pend_em = pend_tr = false;
+        }
         n = 0; X = 0.f; Y = 0.f; Sx = 0.f; Z = 0.f; XI = 0.f;
       }
       if (base + cnt >= pend) ++want;
@@ -375,10 +392,14 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
     idle_since = 0;
 
     // ---- step until a warp of the group has gathered enough exits ---------
-    const float h = P.h, sqh = P.sqh;
+    const float h = EXT ? h_l : P.h, sqh = EXT ? sqh_l : P.sqh;
     const float hl2 = h * 1.44269504088896341f;
-    const int kmax = (int)min(P.kmax, (int64_t)0x7fffffff);
+    const int kmax = (int)min(EXT ? kmax_l : P.kmax, (int64_t)0x7fffffff);
     bool exited = false, trunc = false;
+    if constexpr (kMixed) {
+      exited = alive && pend_em;
+      trunc = pend_tr;
+    }
     for (;;) {
       const bool go = alive && !exited;
       float z[4] = {0.f, 0.f, 0.f, 0.f};
@@ -394,7 +415,9 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
         // the network at the step's starting point; while the forward product
         // runs, the step itself (the path does not depend on the network)
         net_grad_start(N, W, g, t, tm, tl, xk + X, yk + Y);
-        const bool stepping_now = go && !exited;
+        // a Philox call serves steps 2q and 2q + 1; a mixed-run path that
+        // resumes at an odd step takes the second half of its call
+        const bool stepping_now = go && !exited && (!kMixed || half >= (n & 1));
         float fac = 0.f, dWx = 0.f, dWy = 0.f;
         if (stepping_now) {
           const Stage& H = S.st(st);
@@ -413,6 +436,11 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
           Y = fmaf(ssh, zb, fmaf(ddy, h, Y));
           ++n;
           exited = (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+          if constexpr (EXT && !const_sigma<COEF>()) {
+            if (exited && gmc > 0.f)
+              exited = gm_outside<COEF>(H, S.tile(st, 0), S.tile(st, 1), xk, yk, X, Y, gmc,
+                                        P.trig_direct);
+          }
           if (!exited && n >= kmax) { exited = true; trunc = true; }
         }
         float gx, gy;
@@ -428,23 +456,83 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
 
     // ---- resolve the exits (Eq. 22-25, corner rule of Sec. 3.3) -----------
     const bool leaving = alive && exited;
+    bool gm_rec = false;  // a Gobet-Menozzi exit of a mixed run: recorded, the path goes on
+    if constexpr (kMixed) gm_rec = leaving && gm_phase;
     ExitResult E;
     if (leaving)
-      E = resolve_exit<COEF, RECORD, 1, false>(S, P, st, xk, yk, X, Y, Sx, Z, XI, trunc, bx0,
-                                                 bx1, by0, by1, 0.f, false);
+      E = resolve_exit<COEF, RECORD, 1, EXT>(S, P, st, xk, yk, X, Y, Sx, Z, XI, trunc, bx0, bx1,
+                                               by0, by1, gmc, gm_rec);
+    if constexpr (EXT) {
+      // RBF stencils (Eq. 21-22): the warp serves one exiting lane at a time,
+      // a stencil knot per lane (as in path_kernel)
+      unsigned pend = __ballot_sync(kFull, E.rbf_exit);
+      while (pend) {
+        const int src = __ffs(pend) - 1;
+        const int r_st = __shfl_sync(kFull, st, src);
+        const int r_side = __shfl_sync(kFull, E.side, src);
+        const float r_s = __shfl_sync(kFull, E.sl, src);
+        const float r_Y = __shfl_sync(kFull, E.Yk, src);
+        bool r_gm = false;
+        if constexpr (kMixed) r_gm = __shfl_sync(kFull, gm_rec ? 1 : 0, src) != 0;
+        const Stage& H = S.st(r_st);
+        const KnotDesc& kd = H.kd;
+        const ProbDesc& D = prob_desc(P, H.prob);
+        const bool vertical = (r_side == 0 || r_side == 2);
+        const int a = kd.a[r_side];
+        const int L = kd.b[r_side] - a + 1;
+        const int lmax = vertical ? H.LY : H.LX;
+        float tau;
+        const float* cf = rbf_interval(D, vertical ? 1 : 0, L, r_s, tau);
+        unsigned long long* acc = S.acc(r_st);
+        double dsum = 0.0;
+        if (cf == nullptr && lane == 0) atomicExch(&P.scratch->error, (int)PDDS_EINVAL);
+        for (int j = lane; cf != nullptr && j < L; j += 32) {
+          const float w = r_Y * rbf_cardinal(cf, L, D.rbf_deg + 1, j, tau);
+          const int tl2 = a + j;
+          if (tl2 == 0 || tl2 == lmax) {
+            const int li = vertical ? kd.line[r_side] : tl2;
+            const int lj = vertical ? tl2 : kd.line[r_side];
+            dsum += (double)w * (double)g_value<COEF>(H, fmaf((float)li, H.dx, H.x0),
+                                                      fmaf((float)lj, H.dy, H.y0));
+          } else if (!r_gm) {
+            atomicAdd(acc + kd.off[r_side] + j, (unsigned long long)__float2ll_rn(w * kFixedOne));
+          }
+        }
+        dsum = warp_sum(dsum);
+        if (lane == src) E.bc += dsum;
+        pend &= pend - 1;
+      }
+    }
     if (leaving) {
-      my_steps += (unsigned long long)n;
-      my_paths += 1;
-      my_trunc += (E.flags & 1);
-      my_clamp += (E.flags >> 1) & 1;
-      if constexpr (RECORD) write_record(S, P, st, kk, p, n, E, XI, false);
-      atomicAdd(&S.st(st).bsum, E.bc);
+      if (!gm_rec) {
+        my_steps += (unsigned long long)n;
+        my_paths += 1;
+        my_trunc += (E.flags & 1);
+        my_clamp += (E.flags >> 1) & 1;
+      }
+      if constexpr (RECORD) write_record(S, P, st, kk, p, n, E, XI, gm_rec);
+      if (!gm_rec) atomicAdd(&S.st(st).bsum, E.bc);
+    }
+    if constexpr (kMixed) {
+      if (gm_rec) {
+        // on to the naive exit: the closed patch, no shift
+        const KnotDesc& kd = S.st(st).kd;
+        gm_phase = false;
+        gmc = 0.f;
+        bx0 = kd.box[0]; bx1 = kd.box[1]; by0 = kd.box[2]; by1 = kd.box[3];
+        // a GM exit on the step cap, still inside the patch, is the naive
+        // path's truncation at that same step
+        pend_tr = trunc || n >= kmax;
+        pend_em = pend_tr || (X > bx1) | (X < bx0) | (Y > by1) | (Y < by0);
+      } else if (leaving) {
+        pend_em = pend_tr = false;
+      }
     }
     // warp-aggregated completion counts per stage; the warp that finishes a
     // unit flushes it and loads the next one (bounded waits only)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const unsigned m = __ballot_sync(kFull, leaving && st == s);
+      const unsigned m = __ballot_sync(kFull, leaving && !gm_rec && st == s);
       if (m == 0) continue;
       __syncwarp();
       __threadfence_block();
@@ -458,12 +546,12 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
       if (fin) {
         const int q = (int)(ctrl_state(&S.st(s).ctrl) >> 1);
         flush_unit(S, s, P);
-        if (!load_unit<false>(S, s, q + 2, P, total_units, units_done)) ok = false;
+        if (!load_unit<EXT>(S, s, q + 2, P, total_units, units_done)) ok = false;
         if (lane == 0) atomicSub(S.live, 1);
         __syncwarp();
       }
     }
-    if (leaving) alive = false;
+    if (leaving && !gm_rec) alive = false;
   }
 
   my_steps = warp_sum_u64(my_steps);

@@ -19,8 +19,9 @@ namespace pdds {
 // and its launch with the network's FP32 vectors (host, 5 x 64: W1[:, 0],
 // W1[:, 1], b1, b2, w3) as a kernel parameter (pdds_path_net.cu).
 size_t net_smem_bytes();
-cudaError_t launch_path_kernel_net(int coef, bool rec, const KParams& kp, const float* w,
-                                   int grid, int block, size_t smem, cudaStream_t stream);
+cudaError_t launch_path_kernel_net(int coef, bool rec, bool ext, const KParams& kp,
+                                   const float* w, int grid, int block, size_t smem,
+                                   cudaStream_t stream);
 }  // namespace pdds
 
 using pdds::KnotDesc;
@@ -462,9 +463,9 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   const double kmax_eff = ext && c->d_hknot && c->h_min < dt ? (double)kmax * dt / c->h_min
                                                              : (double)kmax;
   kp.wait_ns = c->wait_s > 0 ? (uint64_t)(c->wait_s * 1e9) : (uint64_t)(10e9 + 4000.0 * kmax_eff);
-  // cv 3: the in-path network on tcgen05 (warpgroup kernel, naive exit only)
+  // cv 3: the in-path network on tcgen05 (the warpgroup kernel)
   int cv = nprob == 1 ? c->cv_mode : 0;
-  if (cv == 1 && !ext && c->net_engine == PDDS_NET_TCGEN05) cv = 3;
+  if (cv == 1 && c->net_engine == PDDS_NET_TCGEN05) cv = 3;
   kp.mlp = cv == 1 || cv == 3 ? c->d_mlp : nullptr;
   {
     // the largest |coordinate| of the launch's domains (problem 0 here, the
@@ -502,8 +503,8 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
   c->st.path_block = block;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, stream));
   if (cv == 3)
-    CK(c, pdds::launch_path_kernel_net(coef_id, rec != nullptr, kp, c->net_w, grid, block, smem,
-                                       stream));
+    CK(c, pdds::launch_path_kernel_net(coef_id, rec != nullptr, ext, kp, c->net_w, grid, block,
+                                       smem, stream));
   else
     CK(c, pdds::launch_path_kernel(coef_id, rec != nullptr, cv, ext, kp, grid, block, smem, stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, stream));
@@ -863,9 +864,8 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   static std::map<Key, Shape> cache;
   // xk: the extended-exit kernel (GM scheme or per-knot steps) is a different kernel
   const int xk = (c->scheme == PDDS_SCHEME_GM ? 1 : 0) + (c->d_hknot ? 2 : 0);
-  // the in-path network on tcgen05 (naive exit) is its own kernel too
-  const bool net_tc = c->cv_mode == 1 && xk == 0 && c->interp != PDDS_INTERP_RBF &&
-                      c->net_engine == PDDS_NET_TCGEN05;
+  // the in-path network on tcgen05 is its own kernel too
+  const bool net_tc = c->cv_mode == 1 && c->net_engine == PDDS_NET_TCGEN05;
   const Key key{c->device, c->coef_id, net_tc ? 3 : c->cv_mode, xk, c->grid.Hx, c->grid.Hy,
                 c->grid.m, c->grid.ext, n_paths};
   {

@@ -93,12 +93,13 @@ void* path_kernel_cvt(int coef, bool rec);
 void* path_kernel_ext(int coef, bool rec);
 void* path_kernel_ext_cv(int coef, bool rec);
 void* path_kernel_ext_cvt(int coef, bool rec);
-void* path_kernel_net_tc(int coef, bool rec);  // cv 3: the network on tcgen05 (pdds_path_net.cu)
+void* path_kernel_net_tc(int coef, bool rec);      // cv 3: the network on tcgen05 (pdds_path_net.cu)
+void* path_kernel_net_ext_tc(int coef, bool rec);  // the same with the extended exit
 
 namespace {
 void* pick(int coef, bool rec, int cv, bool ext) {
   if (ext) {
-    if (cv == 3) return nullptr;
+    if (cv == 3) return path_kernel_net_ext_tc(coef, rec);
     if (cv == 1) return path_kernel_ext_cv(coef, rec);
     if (cv == 2) return path_kernel_ext_cvt(coef, rec);
     return path_kernel_ext(coef, rec);

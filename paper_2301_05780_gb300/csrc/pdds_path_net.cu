@@ -1,13 +1,14 @@
 // In-path network control variate on the fifth-generation tensor cores
-// (path_kernel_net, naive EM exit): the analytic sets used with a learned
-// v_theta and the constant set, as in pdds_path_cv.cu.
+// (path_kernel_net, naive EM exit; the extended-exit variants are in
+// pdds_path_net_ext.cu): the analytic sets used with a learned v_theta and
+// the constant set, as in pdds_path_cv.cu.
 #include "path_kernel_net.cuh"
 
 namespace pdds {
 namespace {
 template <int COEF, bool REC>
 void* ptr() {
-  return reinterpret_cast<void*>(&path_kernel_net<COEF, REC>);
+  return reinterpret_cast<void*>(&path_kernel_net<COEF, REC, false>);
 }
 }  // namespace
 
@@ -30,9 +31,12 @@ size_t net_smem_bytes() { return (size_t)kNetSmemBytes; }
 
 // w: host array of the network's FP32 vectors, W1[:, 0], W1[:, 1], b1, b2, w3
 // (64 each), passed halved, by value, as the kernel's second parameter.
-cudaError_t launch_path_kernel_net(int coef, bool rec, const KParams& kp, const float* w,
-                                   int grid, int block, size_t smem, cudaStream_t stream) {
-  void* fn = path_kernel_net_tc(coef, rec);
+void* path_kernel_net_ext_tc(int coef, bool rec);  // pdds_path_net_ext.cu
+
+cudaError_t launch_path_kernel_net(int coef, bool rec, bool ext, const KParams& kp,
+                                   const float* w, int grid, int block, size_t smem,
+                                   cudaStream_t stream) {
+  void* fn = ext ? path_kernel_net_ext_tc(coef, rec) : path_kernel_net_tc(coef, rec);
   if (!fn) return cudaErrorInvalidValue;
   NetWeights W;
   for (int u = 0; u < kNetH; ++u) {

@@ -227,6 +227,40 @@ def test_cv_assembly_parity_with_oracle(orc, oracle_theta, engine):
                         b_extra_tol=2e-2 * xi_row)
 
 
+@pytest.mark.parametrize("engine", [pdds.NET_TCGEN05, pdds.NET_MMA_SYNC],
+                         ids=["tcgen05", "mma_sync"])
+def test_cv_gm_knot_steps_parity_with_oracle(orc, oracle_theta, engine):
+    """The network control variate in the extended-exit kernels: Gobet-Menozzi
+    exits and per-knot steps in [h/2, 2h], same streams and theta on both
+    sides; the tolerances of the naive-exit case."""
+    w = _cv_workload(300)
+    P = pdds.Problem(w)
+    pdds.pdds_set_network_engine(P.ctx, engine)
+    pdds.pdds_set_scheme(P.ctx, pdds.PDDS_SCHEME_GM)
+    h = np.random.default_rng(9).uniform(0.5 * w.dt, 2.0 * w.dt, P.n)
+    pdds.pdds_set_knot_steps(P.ctx, torch.tensor(h, dtype=torch.float64, device="cuda"))
+    pdds.pdds_set_control_variate(P.ctx, dev32(oracle_theta))
+    rec = P.records_buffer()
+    P.assemble(records=rec)
+    torch.cuda.synchronize()
+    assert pdds.pdds_stats(P.ctx)["device_error"] == 0
+    g = dict(row_ptr=P.row_ptr.cpu().numpy(), col=P.col.cpu().numpy(), val=P.val.cpu().numpy(),
+             b=P.b.cpu().numpy(), rec=pdds.records_to_numpy(rec))
+    O = orc.Problem(w.grid, w.coef_id, w.params)
+    _, _, _, rplain = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, records=True,
+                                 scheme=orc.SCHEME_GM, h_per_knot=h)
+    O.set_mlp(oracle_theta.astype(np.float64))
+    val, b, _, rcv = O.assemble(w.n_paths, w.dt, w.seed, w.k_max, records=True,
+                                scheme=orc.SCHEME_GM, h_per_knot=h)
+    o = dict(row_ptr=O.row_ptr, col=O.col, val=val, b=b, rec=rcv)
+    xi = np.abs(rcv["b_contrib"] - rplain["b_contrib"])
+    n = P.n
+    xi_row = np.bincount(np.repeat(np.arange(n), w.n_paths), weights=xi, minlength=n)
+    assert xi_row.sum() > 0
+    parity.compare_rows(g, o, np.arange(n), np.full(n, w.n_paths), n,
+                        b_extra_tol=2e-2 * xi_row)
+
+
 def test_cv_reduces_variance_and_keeps_the_mean(trained_theta):
     """Per-row sample variance of the path scores drops by > 10x with the
     trained v_theta, and b moves by less than 4 standard errors."""

@@ -194,8 +194,8 @@ def _moments(pe, pg, x, idx, n):
 
 
 @pytest.mark.parametrize("use_cv,k_cap,knot_steps", [
-    (False, None, False), (True, None, False), (False, 60, False), (False, None, True),
-    ("table", None, False)])
+    (False, None, False), (True, None, False), ("mma_sync", None, False), (False, 60, False),
+    (False, None, True), ("table", None, False)])
 def test_calibration_moments_parity(orc, oracle_theta, use_cv, k_cap, knot_steps):
     """pdds_calibrate against the oracle's mixed GM/EM run on the same streams
     and the same u0: flagged paths (step count or side differing in either
@@ -223,12 +223,12 @@ def test_calibration_moments_parity(orc, oracle_theta, use_cv, k_cap, knot_steps
         # a network fitted by the oracle itself: nothing the oracle reads comes
         # from the library
         theta = torch.tensor(oracle_theta, dtype=torch.float32, device="cuda")
-    # GPU: calibration moments, plus the two record passes it is made of.
-    # The calibration's mixed GM/EM run is an extended-exit kernel, which
-    # evaluates the network with the warp-level engine; the naive-exit record
-    # pass below takes the same engine, so that the two agree to the last bit.
+    # GPU: calibration moments, plus the two record passes it is made of (the
+    # in-path network on the tcgen05 engine, or on the warp-level one for
+    # use_cv "mma_sync"; the mixed run and the record passes take the same)
     P = _problem(w, EM, h_per_knot=h_k, theta=theta)
-    pdds.pdds_set_network_engine(P.ctx, pdds.NET_MMA_SYNC)
+    if use_cv == "mma_sync":
+        pdds.pdds_set_network_engine(P.ctx, pdds.NET_MMA_SYNC)
     if tab is not None:
         pdds.pdds_set_control_variate_grid(P.ctx, torch.tensor(tab, device="cuda"))
     mom = torch.empty(n, 8, dtype=torch.float64, device="cuda")
