@@ -422,8 +422,9 @@ pdds_status pdds_set_control_variate(pdds_ctx* ctx, const float* theta);
  *  PDDS_NET_TCGEN05 (default): the paths of a 128-thread warpgroup step
  *    together; at each step the 128 positions form one M = 128 tile, h1 W2^T
  *    and g2 W2 run as tcgen05.mma (kind::f16, BF16 operands, FP32 in TMEM),
- *    SiLU'(a1) waits in TMEM.  Launch: 128 or 256 threads per CTA (block
- *    below 256 gives 128), at most 512 / block CTAs per SM (TMEM columns).
+ *    SiLU'(a1) waits in TMEM as BF16 pairs.  Launch: 128 threads per CTA
+ *    (the block setting of pdds_set_launch does not apply), up to five CTAs
+ *    per SM (96 TMEM columns, 96 registers per thread).
  *    Both exits (naive and extended: Gobet-Menozzi, per-knot steps, RBF
  *    stencils, the calibration's mixed run).  Each wait for a product is
  *    bounded by max(wait limit, 1 s) (pdds_set_wait_limit).

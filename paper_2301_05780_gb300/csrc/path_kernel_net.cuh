@@ -40,9 +40,9 @@ constexpr int kNetH = kMlpHidden;
 struct alignas(1024) NetSmem {
   uint16_t B1[kNetH * kNetH];  // W2 as N = out x K = in
   uint16_t B2[kNetH * kNetH];  // W2^T as N = in x K = out
-  uint16_t A[2][kNetRows * kNetH];
-  unsigned long long mbar[2];
-  unsigned tmem;
+  uint16_t A[kNetRows * kNetH];
+  unsigned long long mbar;
+  unsigned tmem, tmem_s1;  // TMEM: the products (64 columns), 2 SiLU'(a1) as BF16 pairs (32)
 };
 // + alignment slack: the dynamic shared memory is aligned by hand
 constexpr int kNetSmemBytes = (int)((sizeof(NetSmem) + 1024 + 127) / 128 * 128);
@@ -134,8 +134,9 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 // group's mbarrier parity, flipped twice by net_grad_finish, whose wait_ns
 // bounds each wait for a product.  The SIMT parts work on unit pairs (f32x2).
 __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, int g, int t,
-                                               unsigned tm, unsigned tl, float x, float y) {
-  uint16_t* const A = N.A[g];
+                                               unsigned tm, unsigned ts, unsigned tl, float x,
+                                               float y) {
+  uint16_t* const A = N.A;
   char* const Ab = reinterpret_cast<char*>(A);
   __syncwarp();  // the tcgen05 loads and stores below are warp-aligned
   // layer 1: h1 into row t of the A tile, SiLU'(a1) into TMEM
@@ -159,7 +160,10 @@ __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, 
       }
       *reinterpret_cast<uint4*>(Ab + net_chunk(t, 2 * q + c2)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
     }
-    tc::tmem_st16(tm + tl + 64 + 16 * q, d);
+    uint32_t dp[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) dp[j] = bf16x2(d[2 * j], d[2 * j + 1]);
+    tc::tmem_st8u(ts + tl + 8 * q, dp);
   }
   tc::st_wait();
   tc::fence_async_smem();
@@ -168,7 +172,7 @@ __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, 
   if (t == 0) {
     tc::fence_after();
     net_mma(tm, A, N.B1);
-    tc::commit(&N.mbar[g]);
+    tc::commit(&N.mbar);
   }
 }
 
@@ -176,11 +180,12 @@ __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, 
 // product, then layer 2, the backward product and the input gradient.
 // Returns false if a wait ran out (results void).
 __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W, int g, int t,
-                                                unsigned tm, unsigned tl, unsigned& phase,
+                                                unsigned tm, unsigned ts, unsigned tl,
+                                                unsigned& phase,
                                                 uint64_t wait_ns, float& gx, float& gy) {
-  uint16_t* const A = N.A[g];
+  uint16_t* const A = N.A;
   char* const Ab = reinterpret_cast<char*>(A);
-  bool ok = net_wait(&N.mbar[g], phase, wait_ns);
+  bool ok = net_wait(&N.mbar, phase, wait_ns);
   phase ^= 1u;
   tc::fence_after();
   // dv/da2 = w3 SiLU'(a2) into the A tile (the forward product has read it)
@@ -210,9 +215,9 @@ __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W,
   if (t == 0) {
     tc::fence_after();
     net_mma(tm, A, N.B2);
-    tc::commit(&N.mbar[g]);
+    tc::commit(&N.mbar);
   }
-  ok = net_wait(&N.mbar[g], phase, wait_ns) && ok;
+  ok = net_wait(&N.mbar, phase, wait_ns) && ok;
   phase ^= 1u;
   tc::fence_after();
   // grad v = W1^T (dv/dh1 * SiLU'(a1)) = (W1/2)^T (dv/dh1 * 2 SiLU'(a1)), even
@@ -221,8 +226,14 @@ __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W,
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float dh[16], s1[16];
+    uint32_t sp[8];
     tc::tmem_ld16(tm + tl + 16 * q, dh);
-    tc::tmem_ld16(tm + tl + 64 + 16 * q, s1);
+    tc::tmem_ld8u(ts + tl + 8 * q, sp);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      s1[2 * j] = __uint_as_float(sp[j] << 16);
+      s1[2 * j + 1] = __uint_as_float(sp[j] & 0xffff0000u);
+    }
 #pragma unroll
     for (int j = 0; j < 16; j += 2) {
       const int u = 16 * q + j;
@@ -236,17 +247,17 @@ __device__ __forceinline__ bool net_grad_finish(NetSmem& N, const NetWeights& W,
   return ok;
 }
 
-// Threads per CTA: one or two warpgroups; TMEM: 128 columns per group (64 for
-// the products, 64 for SiLU'(a1)), so at most 512 / (128 groups) CTAs per SM.
+// One warpgroup (128 threads) per CTA; TMEM: 64 columns for the products and
+// 32 for 2 SiLU'(a1) as BF16 pairs (the rounding the warp-level routine gives
+// it too), so five CTAs per SM fit in TMEM, registers (96) and shared memory.
 template <int COEF, bool RECORD, bool EXT>
-__global__ void __launch_bounds__(2 * kNetRows, 2)
+__global__ void __launch_bounds__(kNetRows, 5)
     path_kernel_net(const __grid_constant__ KParams P, const __grid_constant__ NetWeights W) {
   extern __shared__ __align__(128) char smem_raw[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int g = tid / kNetRows, t = tid % kNetRows;
-  const int ngroups = (int)(blockDim.x / kNetRows);
+  const int g = 0, t = tid;  // one warpgroup per CTA (named barrier 1)
   // 1024-byte aligned by an offset from the shared array itself, so that the
   // compiler keeps every access in the shared state space
   char* const nbase = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -285,9 +296,12 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
       S.st(s).tma_phase = 0;
       mbar_init(&S.st(s).mbar);
     }
-    for (int q = 0; q < ngroups; ++q) tc::mbar_init(&N.mbar[q]);
+    tc::mbar_init(&N.mbar);
   }
-  if (warp == 0) tc::tmem_alloc(&N.tmem, 128u * (unsigned)ngroups);
+  if (warp == 0) {
+    tc::tmem_alloc_more(&N.tmem, 64u);
+    tc::tmem_alloc(&N.tmem_s1, 32u);
+  }
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
   bool ok = true;
   if (warp < 2) ok = load_unit<EXT>(S, warp, warp, P, total_units, units_done);
   __syncthreads();
-  const unsigned tm = N.tmem + 128u * (unsigned)g;
+  const unsigned tm = N.tmem, ts = N.tmem_s1;
   const unsigned tl = (unsigned)((warp & 3) * 32) << 16;
   unsigned phase = 0;
 
@@ -414,7 +428,7 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
         const float za = half ? z[2] : z[0], zb = half ? z[3] : z[1];
         // the network at the step's starting point; while the forward product
         // runs, the step itself (the path does not depend on the network)
-        net_grad_start(N, W, g, t, tm, tl, xk + X, yk + Y);
+        net_grad_start(N, W, g, t, tm, ts, tl, xk + X, yk + Y);
         // a Philox call serves steps 2q and 2q + 1; a mixed-run path that
         // resumes at an odd step takes the second half of its call
         const bool stepping_now = go && !exited && (!kMixed || half >= (n & 1));
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
           if (!exited && n >= kmax) { exited = true; trunc = true; }
         }
         float gx, gy;
-        if (!net_grad_finish(N, W, g, t, tm, tl, phase, mma_wait_ns, gx, gy)) ok = false;
+        if (!net_grad_finish(N, W, g, t, tm, ts, tl, phase, mma_wait_ns, gx, gy)) ok = false;
         // dxi = -Y s grad v . dW at the step's starting point (Eq. 37)
         if (stepping_now) XI = fmaf(fac, fmaf(gx, dWx, gy * dWy), XI);
       }
@@ -570,7 +584,8 @@ __global__ void __launch_bounds__(2 * kNetRows, 2)
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(N.tmem, 128u * (unsigned)ngroups);
+    tc::tmem_dealloc(N.tmem, 64u);
+    tc::tmem_dealloc(N.tmem_s1, 32u);
   }
 }
 

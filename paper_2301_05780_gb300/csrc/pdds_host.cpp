@@ -488,16 +488,15 @@ pdds_status run_paths(pdds_ctx* c, const ProbDesc& p0, const ProbDesc* d_probs, 
                                     : cv == 3 ? pdds::net_smem_bytes()
                                               : 0);
   CK(c, pdds::set_path_kernel_smem(coef_id, rec != nullptr, cv, ext, smem));
-  // network: <= 256 threads; the tcgen05 kernel takes one or two warpgroups
-  const int block = cv == 1 ? std::min(c->block, 256) : cv == 3 ? (c->block >= 256 ? 256 : 128)
-                                                                : c->block;
+  // network: <= 256 threads; the tcgen05 kernel takes one warpgroup
+  const int block = cv == 1 ? std::min(c->block, 256) : cv == 3 ? 128 : c->block;
   int per_sm = c->ctas_per_sm;
   if (per_sm <= 0) {
     CK(c, pdds::path_kernel_occupancy(coef_id, rec != nullptr, cv, ext, block, smem, &per_sm));
     if (per_sm <= 0) return fail(c, PDDS_EINVAL, "launch: block/shared memory too large");
   }
-  // tcgen05 kernel: 128 TMEM columns per warpgroup, 512 per SM
-  if (cv == 3) per_sm = std::min(per_sm, 512 / block);
+  // tcgen05 kernel: 96 TMEM columns per CTA, 512 per SM
+  if (cv == 3) per_sm = std::min(per_sm, 512 / 96);
   const int grid = c->num_sms * per_sm;
   c->st.path_grid = grid;
   c->st.path_block = block;
@@ -920,7 +919,7 @@ pdds_status pdds_autotune(pdds_ctx* c, int64_t n_paths, double dt, uint64_t seed
   for (int bl : blocks)
     for (int un : units)
       for (int ba : batches)
-        if (!(c->cv_mode == 1 && bl > 256) && !(net_tc && bl < 128))
+        if (!(c->cv_mode == 1 && bl > 256) && !(net_tc && bl != 128))
           shapes.push_back(Shape{bl, un, ba});
   auto time_shape = [&](const Shape& sh, const int64_t* N, int64_t Nu, float& ms) {
     c->block = sh.block;

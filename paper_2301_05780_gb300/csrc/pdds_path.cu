@@ -144,7 +144,7 @@ cudaError_t path_kernel_occupancy(int coef, bool rec, int cv, bool ext, int bloc
   const int regs = (fa.numRegs + 7) / 8 * 8;  // allocated per warp in 256-register steps
   const int by_regs = regs_sm / (regs * block);
   const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + (size_t)smem_res);
-  const int by_tmem = 512 / block;  // 128 TMEM columns per 128-thread warpgroup
+  const int by_tmem = 512 / 96;  // 64 + 32 TMEM columns per 128-thread CTA
   *ctas = std::max(0, std::min(std::min(by_regs, by_smem), by_tmem));
   return cudaSuccess;
 }
