@@ -57,7 +57,9 @@ struct alignas(1024) TrainTcSmem {
   uint16_t GA[kGR * kTT];   // gradient A: unit rows x K = point (two 64-point atom columns)
   uint16_t GB[kBR * kTT];   // gradient B: h1^T, x, y, 1, zeros
   uint16_t DV[kVR * kTT];   // dv, zeros
-  float w1x[kHU], w1y[kHU], b1[kHU], b2[kHU], w3[kHU];
+  // W1[:, 0], W1[:, 1], b1, b2 and w3 halved (the SiLU algebra works with
+  // a/2), w3 as it is (v)
+  float w1xh[kHU], w1yh[kHU], b1h[kHU], b2h[kHU], w3h[kHU], w3[kHU];
   float b3;
   float red_v[2][kTT];  // the two groups' parts of v
   float red_b3[kThreads / 32];
@@ -79,25 +81,36 @@ __device__ __forceinline__ void put_bf16(uint16_t* tile, int off, float v) {
   *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(tile) + off) = __float2bfloat16_rn(v);
 }
 
-// Parameter i of theta into the shared-memory image (W2 as the two BF16 B
-// operands).
+// Parameter i of theta into the shared-memory image: W2 as the two BF16 B
+// operands (the forward one halved, so that the product gives a2/2; halving
+// is exact), the vectors of the SiLU algebra halved.
 __device__ __forceinline__ void stage_tc(TrainTcSmem& S, int i, float w) {
   if (i < kOffB1) {
-    if (i & 1) S.w1y[i >> 1] = w;
-    else S.w1x[i >> 1] = w;
+    if (i & 1) S.w1yh[i >> 1] = 0.5f * w;
+    else S.w1xh[i >> 1] = 0.5f * w;
   } else if (i < kOffW2) {
-    S.b1[i - kOffB1] = w;
+    S.b1h[i - kOffB1] = 0.5f * w;
   } else if (i < kOffB2) {
     const int j = i - kOffW2, o = j >> 6, u = j & 63;
-    put_bf16(S.W2o, bo(o, u, kHU), w);
+    put_bf16(S.W2o, bo(o, u, kHU), 0.5f * __bfloat162float(__float2bfloat16_rn(w)));
     put_bf16(S.W2t, bo(u, o, kHU), w);
   } else if (i < kOffW3) {
-    S.b2[i - kOffB2] = w;
+    S.b2h[i - kOffB2] = 0.5f * w;
   } else if (i < kOffB3) {
     S.w3[i - kOffW3] = w;
+    S.w3h[i - kOffW3] = 0.5f * w;
   } else {
     S.b3 = w;
   }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 tanh2(float2 a) { return f2(tanh_approx(a.x), tanh_approx(a.y)); }
+// With a' = a/2 and t = tanh(a'): SiLU(a) = a' (1 + t), and
+// SiLU'(a) = (1 + u) / 2 with u = t + a' (1 - t^2).
+__device__ __forceinline__ float2 silu_u(float2 a, float2 t) {
+  return __ffma2_rn(a, __ffma2_rn(t, f2(-t.x, -t.y), f2(1.0f, 1.0f)), t);
 }
 
 // D [+]= A B^T over nk K-steps of 16 points or units; A and B K-major with Ra
@@ -225,13 +238,15 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_train_tc_kernel(const TrainAr
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int u = 16 * q + 8 * c2 + 2 * j;
-          float h0, d0, h1, d1;
-          silu_and_slope(fmaf(S.w1x[u], x, fmaf(S.w1y[u], y, S.b1[u])), h0, d0);
-          silu_and_slope(fmaf(S.w1x[u + 1], x, fmaf(S.w1y[u + 1], y, S.b1[u + 1])), h1, d1);
-          if (!valid) { h0 = 0.f; h1 = 0.f; }
+          const float2 a = __ffma2_rn(ld2(&S.w1xh[u]), f2(x, x),
+                                      __ffma2_rn(ld2(&S.w1yh[u]), f2(y, y), ld2(&S.b1h[u])));
+          const float2 t = tanh2(a);
+          const float2 h = __ffma2_rn(a, t, a);                                    // SiLU(a1)
+          const float2 d = __ffma2_rn(f2(0.5f, 0.5f), silu_u(a, t), f2(0.5f, 0.5f));  // SiLU'
+          const float h0 = valid ? h.x : 0.f, h1 = valid ? h.y : 0.f;
           hp[j] = pack_bf16x2(h0, h1);
-          s1[8 * c2 + 2 * j] = d0;
-          s1[8 * c2 + 2 * j + 1] = d1;
+          s1[8 * c2 + 2 * j] = d.x;
+          s1[8 * c2 + 2 * j + 1] = d.y;
           put_bf16(S.GB, bo(u, pl, kBR), h0);
           put_bf16(S.GB, bo(u + 1, pl, kBR), h1);
         }
@@ -260,23 +275,26 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_train_tc_kernel(const TrainAr
     tc::fence_after();
     // ---- output: h2^T (column pl) and the group's part of v; then v, the
     // residual, dv, and g2 into P and g2^T
-    float s2[32];
-    float vpart = 0.f;
+    float2 us[16];  // u of each unit pair: SiLU'(a2) = (1 + u) / 2
+    float2 vp = f2(0.f, 0.f);
 #pragma unroll
     for (int qq = 0; qq < 2; ++qq) {
       const int q = 2 * g + qq;
       float a2[16];
-      tc::tmem_ld16(tm + tl + kColD + 16 * q, a2);
+      tc::tmem_ld16(tm + tl + kColD + 16 * q, a2);  // a2 / 2 - b2 / 2
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < 16; j += 2) {
         const int o = 16 * q + j;
-        float h;
-        silu_and_slope(a2[j] + S.b2[o], h, s2[16 * qq + j]);
-        vpart = fmaf(S.w3[o], h, vpart);
-        put_bf16(S.GA, bo(128 + o, pl, kGR), h);
+        const float2 a = __fadd2_rn(f2(a2[j], a2[j + 1]), ld2(&S.b2h[o]));
+        const float2 t = tanh2(a);
+        const float2 h = __ffma2_rn(a, t, a);  // SiLU(a2)
+        us[8 * qq + j / 2] = silu_u(a, t);
+        vp = __ffma2_rn(ld2(&S.w3[o]), h, vp);
+        put_bf16(S.GA, bo(128 + o, pl, kGR), h.x);
+        put_bf16(S.GA, bo(128 + o + 1, pl, kGR), h.y);
       }
     }
-    S.red_v[g][pl] = vpart;
+    S.red_v[g][pl] = vp.x + vp.y;
     __syncthreads();
     const float vs = S.b3 + S.red_v[0][pl] + S.red_v[1][pl];  // the same in both groups
     const float r = valid ? vs - tg : 0.f;
@@ -292,8 +310,10 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_train_tc_kernel(const TrainAr
       uint32_t gp[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int o = 8 * c + 2 * j, k = 8 * cc + 2 * j;
-        const float g0 = dv * S.w3[o] * s2[k], g1 = dv * S.w3[o + 1] * s2[k + 1];
+        const int o = 8 * c + 2 * j;
+        const float2 dw = __fmul2_rn(ld2(&S.w3h[o]), f2(dv, dv));
+        const float2 gg = __ffma2_rn(dw, us[4 * cc + j], dw);  // dv w3 SiLU'(a2)
+        const float g0 = gg.x, g1 = gg.y;
         gp[j] = pack_bf16x2(g0, g1);
         put_bf16(S.GA, bo(o, pl, kGR), g0);
         put_bf16(S.GA, bo(o + 1, pl, kGR), g1);

@@ -227,6 +227,31 @@ def test_cv_assembly_parity_with_oracle(orc, oracle_theta, engine):
                         b_extra_tol=2e-2 * xi_row)
 
 
+def test_network_engine_setting_and_launch_shape():
+    """pdds_set_network_engine: an unknown engine is refused (EINVAL) and
+    changes nothing; the tcgen05 kernel runs 128-thread CTAs, five per SM
+    (TMEM, registers and shared memory), whatever block the launch asks for."""
+    w = _cv_workload(64)
+    P = pdds.Problem(w)
+    with pytest.raises(pdds.PddsError) as e:
+        pdds.pdds_set_network_engine(P.ctx, 7)
+    assert e.value.status == pdds.PDDS_EINVAL
+    pdds.pdds_set_control_variate(P.ctx, dev32(W.mlp_init()))
+    pdds.pdds_set_launch(P.ctx, 256, 0, 1024, 4)
+    P.assemble()
+    torch.cuda.synchronize()
+    st = pdds.pdds_stats(P.ctx)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert st["device_error"] == 0 and st["path_block"] == 128, st
+    assert st["path_grid"] == 5 * sms, (st["path_grid"], sms)
+    pdds.pdds_set_network_engine(P.ctx, pdds.NET_MMA_SYNC)
+    P.assemble()
+    torch.cuda.synchronize()
+    st = pdds.pdds_stats(P.ctx)
+    assert st["device_error"] == 0 and st["path_block"] == 256, st
+    P.close()
+
+
 @pytest.mark.parametrize("engine", [pdds.NET_TCGEN05, pdds.NET_MMA_SYNC],
                          ids=["tcgen05", "mma_sync"])
 def test_cv_gm_knot_steps_parity_with_oracle(orc, oracle_theta, engine):
