@@ -519,8 +519,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="Adam steps of the e1 pipeline's network fit")
     ap.add_argument("--launch", default=None,
-                    help="cfg5_network: fixed launch shape 'block,unit_paths,exit_batch' "
-                         "(no autotune; profiling runs)")
+                    help="cfg5_network, e1: fixed launch shape 'block,unit_paths,exit_batch' "
+                         "(cfg5_network: no autotune; profiling runs)")
     ap.add_argument("--net-engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
                     help="tensor-core engine of the in-path network (cfg5_network)")
     ap.add_argument("--train-engine", default="tc", choices=["fp32", "tc"],
@@ -900,7 +900,8 @@ def run_e1(args):
     x = w.extra
     kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
               rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps,
-              boundary_samples=args.fit_data == "knots+boundary", train_engine=args.train_engine)
+              boundary_samples=args.fit_data == "knots+boundary", train_engine=args.train_engine,
+              launch=tuple(int(v) for v in args.launch.split(",")) if args.launch else None)
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []

@@ -74,7 +74,7 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
         h0p: float | None = None, control_variate: bool = True, train_steps: int = 1500,
         lr: float = 3e-3, solve_rtol: float = 1e-10, rbf: bool = False,
         rbf_shape: float = 0.0, cv_kind: str = "table", boundary_samples: bool = True,
-        train_engine: str = "tc") -> dict:
+        train_engine: str = "tc", launch: tuple | None = (128, 1024, 4)) -> dict:
     """The three phases on workload w (its grid, coefficients and seed; its dt
     and step cap should be those of h0).  rbf: IMQ RBF stencils (Sec. 2.1)
     instead of linear ones, shape rbf_shape (<= 0: cond(Phi) = 1e10).
@@ -84,6 +84,11 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     boundary_samples: the fit also sees g at the boundary points of the
     lattice (pdds_boundary_samples), where u is known exactly.
     train_engine: the fit's training kernel ("fp32" or "tc", fit_network).
+    launch: (block, unit_paths, exit_batch) of the path kernels, or None for
+    the library's default (256, 4096, 4).  The default here was measured on
+    the paper's problem, one GB300, over 15 shapes: 152 ms per pipeline
+    against 173 ms with the library's default (budgets of ~1,300 paths per
+    knot fill units of 1024 and give each CTA's two-stage ring short units).
     Returns the nodal solutions of Phases I and III, the calibration (h_i,
     N_i, gap, var, rho^2), per-phase wall times (CUDA-synchronized) and
     path-step counts."""
@@ -91,6 +96,8 @@ def run(w: W.Workload, eps: float, n0: int, h0: float, n_job: int, n0p: int | No
     n0p = n0 if n0p is None else n0p
     h0p = h0 if h0p is None else h0p
     P = pdds.Problem(w)
+    if launch is not None:
+        pdds.pdds_set_launch(P.ctx, int(launch[0]), 0, int(launch[1]), int(launch[2]))
     dev = P.dev
     n = P.n
     out = {"workload": w.name, "knots": n, "eps": eps, "n0": n0, "h0": h0, "n0p": n0p,
