@@ -33,8 +33,8 @@ namespace {
 constexpr int kNetRows = 128;  // paths per warpgroup = MMA M
 constexpr int kNetH = kMlpHidden;
 
-// The network as the tensor cores read it (per CTA), and one A tile per
-// warpgroup.  BF16 tiles are K-major with the 128-byte swizzle: one 128-byte
+// The network as the tensor cores read it (per CTA), and the warpgroup's A
+// tile.  BF16 tiles are K-major with the 128-byte swizzle: one 128-byte
 // row per point (64 BF16), 8-row groups 1024 bytes apart, the 16-byte chunk c
 // of row r at chunk position c ^ (r % 8).
 struct alignas(1024) NetSmem {
@@ -128,11 +128,12 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 
 // grad v_theta at the thread's point (x, y), in two parts so that the caller
 // can work while the forward product runs: net_grad_start (layer 1, then one
-// thread issues the forward product) and net_grad_finish.  Whole warpgroup g
-// (all 128 threads, converged per warp).  tm: the group's TMEM columns (D at
-// +0, 2 SiLU'(a1) at +64), tl: the warp's TMEM lane offset.  phase: the
-// group's mbarrier parity, flipped twice by net_grad_finish, whose wait_ns
-// bounds each wait for a product.  The SIMT parts work on unit pairs (f32x2).
+// thread issues the forward product) and net_grad_finish.  Whole warpgroup
+// (all 128 threads of the CTA, converged per warp; g names its barrier).  tm:
+// the 64 TMEM columns of the products, ts: the 32 columns of 2 SiLU'(a1) as
+// BF16 pairs, tl: the warp's TMEM lane offset.  phase: the mbarrier parity,
+// flipped twice by net_grad_finish, whose wait_ns bounds each wait for a
+// product.  The SIMT parts work on unit pairs (f32x2).
 __device__ __forceinline__ void net_grad_start(NetSmem& N, const NetWeights& W, int g, int t,
                                                unsigned tm, unsigned ts, unsigned tl, float x,
                                                float y) {
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(kNetRows, 5)
     atomicAdd(&P.scratch->clamped, my_clamp);
     atomicAdd(&P.scratch->units, (unsigned long long)units_done);
   }
-  // TMEM back once both groups are done with it
+  // TMEM back once every warp is done with it
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
