@@ -128,8 +128,8 @@ cudaError_t path_kernel_occupancy(int coef, bool rec, int cv, bool ext, int bloc
   if (cv != 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, block, smem);
   // The tcgen05 network kernel: the occupancy query answers one CTA per SM
   // for it, while registers, shared memory (large carve-out) and tensor
-  // memory admit more (measured: four 128-thread CTAs per SM run 2.3x faster
-  // than one), so the count is taken from those three limits directly.
+  // memory admit five (measured: several 128-thread CTAs per SM run more than
+  // twice as fast as one), so the count is taken from those three limits.
   cudaFuncAttributes fa;
   int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0;
   cudaError_t e = cudaFuncGetAttributes(&fa, fn);
