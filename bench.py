@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import inspect
 import json
 import math
 import os
@@ -900,8 +901,9 @@ def run_e1(args):
     x = w.extra
     kw = dict(eps=x["eps"], n0=args.paths or x["n0"], h0=x["h0"], n_job=x["n_job"],
               rbf=args.interp == "rbf", cv_kind=args.cv, train_steps=args.train_steps,
-              boundary_samples=args.fit_data == "knots+boundary", train_engine=args.train_engine,
-              launch=tuple(int(v) for v in args.launch.split(",")) if args.launch else None)
+              boundary_samples=args.fit_data == "knots+boundary", train_engine=args.train_engine)
+    if args.launch:  # else the pipeline's own launch shape
+        kw["launch"] = tuple(int(v) for v in args.launch.split(","))
     for _ in range(args.warmup):
         calibrated.run(w, **kw)
     runs = []
@@ -926,6 +928,8 @@ def run_e1(args):
                        "interpolation": out["interpolation"], "rbf_shape": out.get("rbf_shape"),
                        "control_variate": args.cv, "train_steps": args.train_steps,
                        "fit_data": args.fit_data, "train_engine": args.train_engine,
+                       "launch": list(kw.get("launch", inspect.signature(calibrated.run)
+                                             .parameters["launch"].default)),
                        "note": "path-steps simulated in the three phases (the calibration's "
                                "mixed GM/EM paths once, to their naive exits)"},
             "pipeline": {
