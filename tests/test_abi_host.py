@@ -87,3 +87,16 @@ def test_record_and_struct_layouts_match_the_header(tmp_path):
     assert grid == ctypes.sizeof(pdds.pdds_grid)
     assert coeffs == ctypes.sizeof(pdds.pdds_coeffs)
     assert stats == ctypes.sizeof(pdds.pdds_stats_t)
+
+
+def test_null_arguments_are_rejected_before_any_cuda_call():
+    """Argument checks that precede every CUDA call (so they run on a machine
+    without a GPU): a NULL context or NULL device pointers give EINVAL."""
+    L = pdds.lib()
+    assert L.pdds_set_network_engine(None, pdds.NET_TCGEN05) == pdds.PDDS_EINVAL
+    assert L.pdds_set_philox_tag(None, 0) == pdds.PDDS_EINVAL
+    assert L.pdds_set_wait_limit(None, 1.0) == pdds.PDDS_EINVAL
+    assert L.pdds_mlp_loss_grad(None, None, None, 10, None, None, None) == pdds.PDDS_EINVAL
+    assert L.pdds_mlp_loss_grad_tc(None, None, None, 10, None, None, None) == pdds.PDDS_EINVAL
+    assert L.pdds_mlp_train_tc(None, None, None, 10, 5, 1e-3, None, None) == pdds.PDDS_EINVAL
+    assert L.pdds_mlp_train(None, None, None, 10, 5, 1e-3, None, None) == pdds.PDDS_EINVAL
